@@ -1,0 +1,166 @@
+/*
+ * splitsolve.h -- C ABI of the GB300 SplitSolve hot path (libsplitsolve.so).
+ *
+ * Problem (Eq. wf, Eq. negf): for each energy E and transverse momentum k,
+ *   (E*S - H - Sigma_L (+) 0 (+) ... (+) Sigma_R) x = Inj
+ * with H Hermitian and S positive definite, both block tridiagonal with n_b
+ * diagonal blocks of size s_b.  The library computes
+ *   - the lead self-energies Sigma_L, Sigma_R by surface-Green's-function
+ *     doubling on the lead cells (decimation, Sec. 3A);
+ *   - the first and last block columns Q of A^-1, A = E*S - H, by the block
+ *     sweeps of Algorithm 1 and its mirror (Sec. 3B, SplitSolve preprocessing);
+ *   - the 2*s_b boundary correction of Eq. x (Steps 1-4, Sherman-Morrison-
+ *     Woodbury with Sigma^RB = B C): R = 1 - C Q, z = R^-1 C y, x = Q (b' + z);
+ *   - the transmission T(E,k) = Re Tr[Gamma_L G_1n Gamma_R G_1n^H],
+ *     Gamma = i (Sigma - Sigma^H).
+ * Every step runs in CUDA kernels on the current device; there is no CPU
+ * fallback: without a usable GPU every call returns SS_ERR_CUDA.
+ *
+ * Conventions
+ *   - complex numbers are interleaved (re, im) float64 pairs (ss_c64);
+ *   - every matrix block is s_b x s_b, row-major, contiguous;
+ *   - arrays holding one entry per point are packed point after point in the
+ *     order of the call's E/k_id arrays (points may have different s_b, n_b);
+ *   - E, k_id, iters and status are HOST arrays; every other array argument
+ *     is a device pointer when cfg.device_ptrs = 1 and a host pointer
+ *     otherwise (host arrays are copied in/out inside the call);
+ *   - all arrays are caller-owned; the library keeps no pointer to them
+ *     after the call returns;
+ *   - every call is enqueued on cfg.stream and synchronises that stream
+ *     before returning (per-point status is reported on the host);
+ *   - every call returns SS_OK (0) or one of the SS_ERR_* codes below and never
+ *     aborts the process; ss_last_error() holds a one-line description.
+ */
+#ifndef SPLITSOLVE_H
+#define SPLITSOLVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } ss_c64;
+typedef struct ss_handle ss_handle;
+
+/* status codes (return values and per-point status entries) */
+#define SS_OK                0
+#define SS_ERR_ARG           1  /* invalid argument (sizes, NULL, unknown k_id shape) */
+#define SS_ERR_STATE         2  /* call order: e.g. no Hamiltonian for a k_id        */
+#define SS_ERR_SINGULAR      3  /* zero or non-finite pivot in a block LU            */
+#define SS_ERR_NOT_CONVERGED 4  /* decimation or refinement hit its iteration cap    */
+#define SS_ERR_TIMEOUT       5  /* a bounded device wait expired                     */
+#define SS_ERR_OOM           6  /* device workspace could not be allocated           */
+#define SS_ERR_CUDA          7  /* CUDA runtime error (no device, launch failure)    */
+
+/* precision modes */
+#define SS_FP64          0  /* every step in FP64                                      */
+#define SS_MIXED_BF16X3  1  /* large GEMMs on tcgen05 tensor cores, BF16 hi/lo split,
+                               FP32 accumulation; FP64 panels, boundary, residual and
+                               iterative refinement                                     */
+#define SS_MIXED_BF16X6  2  /* as above with a 3-term BF16 split (6 products)          */
+
+typedef struct {
+  int n_b_max;        /* largest n_b of any k_id (workspace sizing)                   */
+  int s_b_max;        /* largest s_b of any k_id                                      */
+  int max_points;     /* points processed together in one batch (workspace sizing)    */
+  int max_inj;        /* largest n_inj passed to ss_solve                             */
+  int precision;      /* SS_FP64 / SS_MIXED_*                                         */
+  double eta;         /* lead broadening: z = E + i*eta inside the leads (default 1e-10) */
+  double decim_tol;   /* doubling stops when max(|a|_1,|b|_1) <= decim_tol*|D|_1 (1e-14) */
+  int decim_max_iter; /* doubling cap -> SS_ERR_NOT_CONVERGED (default 100)           */
+  double ir_tol;      /* mixed: refinement stops at ||r||/||Inj|| <= ir_tol (1e-14)    */
+  int ir_max_iter;    /* mixed: refinement cap (default 10)                            */
+  int warm_start;     /* reserved: 1 seeds the surface GF from a trained network       */
+  void* stream;       /* cudaStream_t to enqueue on (NULL = legacy default stream)     */
+  int device_ptrs;    /* 1: array arguments are device pointers                        */
+  int use_graphs;     /* 1: replay decimation iterations from captured CUDA graphs     */
+  int profile;        /* 1: time every kernel launch with CUDA events (eager launches,
+                         no graphs); read the totals with ss_profile_read            */
+} ss_config;
+
+/* Fill *cfg with the defaults listed above (n_b_max = 64, s_b_max = 512,
+ * max_points = 8, max_inj = 64, SS_FP64, host pointers, graphs on, profiling off). */
+void ss_config_default(ss_config* cfg);
+
+/* Create a handle bound to the current CUDA device; allocates the device
+ * workspace for cfg->max_points points of (n_b_max, s_b_max).
+ * Errors: SS_ERR_ARG (NULL or non-positive sizes), SS_ERR_CUDA (no device),
+ * SS_ERR_OOM (workspace does not fit). On error *h is set to NULL. */
+int ss_create(ss_handle** h, const ss_config* cfg);
+
+/* Store the blocks of H(k) and S(k) for momentum index k_id (0 <= k_id < 4096),
+ * replacing any earlier ones.  H_diag, S_diag: n_b*s_b*s_b; H_upper, S_upper:
+ * (n_b-1)*s_b*s_b, block i couples cell i to i+1; lower blocks are the
+ * conjugate transposes.  lead_L / lead_R: NULL for a periodic copy of the end
+ * cell (needs n_b >= 2), else 4*s_b*s_b holding {H00, H01, S00, S01} of the
+ * lead, H01 coupling lead cell q to q+1 (the device-lead coupling is H01).
+ * The data are copied into device memory owned by the handle.
+ * Errors: SS_ERR_ARG (sizes above the handle's maxima, NULL blocks). */
+int ss_set_hamiltonian(ss_handle* h, int k_id, int n_b, int s_b,
+                       const ss_c64* H_diag, const ss_c64* H_upper,
+                       const ss_c64* S_diag, const ss_c64* S_upper,
+                       const ss_c64* lead_L, const ss_c64* lead_R);
+
+/* Lead self-energies at real energies E[p] for the Hamiltonian k_id[p]:
+ * Sigma_L = A_{1,0} g_L A_{0,1}, Sigma_R = A_{n,n+1} g_R A_{n+1,n} (A at real E,
+ * surface Green's functions g at E + i*eta by doubling).  sigma_L/sigma_R
+ * (optional, may be NULL): s_b*s_b per point.  iters (optional, host):
+ * 2 per point (left, right doubling steps).  status (optional, host): per
+ * point SS_OK / SS_ERR_NOT_CONVERGED / SS_ERR_SINGULAR.  The results are
+ * kept in the handle for later ss_solve / ss_transmission on the same
+ * (E, k_id).  Returns the first non-OK point status, or a call-level error. */
+int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id,
+                   ss_c64* sigma_L, ss_c64* sigma_R, int* iters, int* status);
+
+/* Wave functions x = (A - Sigma)^-1 Inj for injections non-zero only in the
+ * first and last block rows (Eq. wf; Steps 1-4 of Eq. x).  inj: per point
+ * 2*s_b x n_inj row-major (rows of block 1, then rows of block n_b).
+ * x: per point (n_b*s_b) x n_inj row-major; may be NULL, in which case only
+ * the factors and G_1n are computed (and cached for ss_transmission).
+ * 1 <= n_inj <= cfg.max_inj.  In the mixed modes x is refined in FP64 until
+ * ||Inj - (A - Sigma) x|| <= ir_tol ||Inj|| (status SS_ERR_NOT_CONVERGED at
+ * the cap).  The transmission of each point is computed on the way and kept
+ * for ss_transmission. */
+int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id,
+             int n_inj, const ss_c64* inj, ss_c64* x, int* status);
+
+/* Transmission T(E,k) = Re Tr[Gamma_L G_1n Gamma_R G_1n^H] per point (T:
+ * n_pts doubles).  err_est (optional): FP64 path: |Im Tr| / max(1,|T|);
+ * mixed path: the relative FP64 residual of the refined solve.  Reuses the
+ * cached results of an immediately preceding ss_solve / ss_self_energy on the
+ * same points; otherwise runs the whole pipeline. */
+int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id,
+                    double* T, double* err_est, int* status);
+
+/* Release every device allocation of the handle (NULL is accepted). */
+int ss_destroy(ss_handle* h);
+
+/* One-line description of the last error on this handle ("" if none);
+ * ss_last_error(NULL) describes the last ss_create failure. */
+const char* ss_last_error(const ss_handle* h);
+
+/* Number of kernel launches the library issued on this handle since
+ * ss_create (graph replays count their kernel nodes). */
+long long ss_launch_count(const ss_handle* h);
+
+/* Kernel kinds for ss_profile_read. */
+#define SS_KERNEL_ZGEMM      0  /* batched complex GEMM (all GEMM-shaped steps)      */
+#define SS_KERNEL_FORM       1  /* elementwise forms / copies                         */
+#define SS_KERNEL_LU_PANEL   2  /* LU panel factorisation                             */
+#define SS_KERNEL_LU_ROW     3  /* LU row swaps + L11^-1 on the row block             */
+#define SS_KERNEL_LU_BACK    4  /* backward substitution in a diagonal block of U     */
+#define SS_KERNEL_NORM1      5  /* matrix 1-norms of the doubling test                */
+#define SS_KERNEL_TRACE      6  /* transmission trace                                 */
+
+/* With cfg.profile = 1: total device time (ms, CUDA events around each
+ * launch on cfg.stream), algorithmic flops (GEMM kind only: 8 m n k per
+ * complex product of every active problem) and launch count of one kernel
+ * kind since ss_create or the last ss_profile_reset.  Errors: SS_ERR_ARG. */
+int ss_profile_read(ss_handle* h, int kind, double* total_ms, double* flops, long long* launches);
+int ss_profile_reset(ss_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLITSOLVE_H */

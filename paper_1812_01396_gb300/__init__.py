@@ -1,0 +1,261 @@
+"""Python binding of libsplitsolve.so (argument marshalling only).
+
+Every computation happens in the CUDA library behind ``include/splitsolve.h``;
+this module converts numpy arrays / torch tensors to pointers and back.  If
+the shared library has not been built, importing still works but every call
+raises ``RuntimeError`` -- there is no CPU fallback.
+
+Names follow the C ABI: :func:`ss_create`, :meth:`Handle.set_hamiltonian`
+(``ss_set_hamiltonian``), :meth:`Handle.self_energy` (``ss_self_energy``),
+:meth:`Handle.solve` (``ss_solve``), :meth:`Handle.transmission`
+(``ss_transmission``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsplitsolve.so")
+
+SS_OK, SS_ERR_ARG, SS_ERR_STATE, SS_ERR_SINGULAR, SS_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+SS_ERR_TIMEOUT, SS_ERR_OOM, SS_ERR_CUDA = 5, 6, 7
+SS_FP64, SS_MIXED_BF16X3, SS_MIXED_BF16X6 = 0, 1, 2
+STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGULAR",
+                4: "SS_ERR_NOT_CONVERGED", 5: "SS_ERR_TIMEOUT", 6: "SS_ERR_OOM", 7: "SS_ERR_CUDA"}
+
+EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
+           "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
+           "ss_profile_reset")
+KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6}
+
+
+class SSConfig(C.Structure):
+    _fields_ = [
+        ("n_b_max", C.c_int), ("s_b_max", C.c_int), ("max_points", C.c_int), ("max_inj", C.c_int),
+        ("precision", C.c_int), ("eta", C.c_double), ("decim_tol", C.c_double),
+        ("decim_max_iter", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
+        ("warm_start", C.c_int), ("stream", C.c_void_p), ("device_ptrs", C.c_int),
+        ("use_graphs", C.c_int), ("profile", C.c_int),
+    ]
+
+
+class SSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the shared library (raises if it is missing: no CPU fallback)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    lib.ss_config_default.argtypes = [C.POINTER(SSConfig)]
+    lib.ss_config_default.restype = None
+    lib.ss_create.argtypes = [C.POINTER(vp), C.POINTER(SSConfig)]
+    lib.ss_set_hamiltonian.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+    lib.ss_self_energy.argtypes = [vp, C.c_int, dp, ip, vp, vp, ip, ip]
+    lib.ss_solve.argtypes = [vp, C.c_int, dp, ip, C.c_int, vp, vp, ip]
+    lib.ss_transmission.argtypes = [vp, C.c_int, dp, ip, vp, vp, ip]
+    lib.ss_destroy.argtypes = [vp]
+    lib.ss_last_error.argtypes = [vp]
+    lib.ss_last_error.restype = C.c_char_p
+    lib.ss_launch_count.argtypes = [vp]
+    lib.ss_launch_count.restype = C.c_longlong
+    lib.ss_profile_read.argtypes = [vp, C.c_int, dp, dp, C.POINTER(C.c_longlong)]
+    lib.ss_profile_read.restype = C.c_int
+    lib.ss_profile_reset.argtypes = [vp]
+    lib.ss_profile_reset.restype = C.c_int
+    for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
+                 "ss_destroy"):
+        getattr(lib, name).restype = C.c_int
+    _lib_handle = lib
+    return lib
+
+
+def ss_config_default() -> SSConfig:
+    cfg = SSConfig()
+    load_library().ss_config_default(C.byref(cfg))
+    return cfg
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _host_c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+class Handle:
+    """Owns one ``ss_handle``.  With ``device_ptrs=True`` array arguments are
+    torch CUDA tensors (complex128 / float64); otherwise numpy arrays."""
+
+    def __init__(self, **kw):
+        lib = load_library()
+        cfg = ss_config_default()
+        for k, v in kw.items():
+            if not hasattr(cfg, k):
+                raise TypeError(f"unknown config field {k}")
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.device_ptrs = bool(cfg.device_ptrs)
+        h = C.c_void_p()
+        rc = lib.ss_create(C.byref(h), C.byref(cfg))
+        if rc != SS_OK:
+            raise SSError(rc, lib.ss_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ss_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self._lib.ss_last_error(self._h).decode()
+
+    def launch_count(self) -> int:
+        return int(self._lib.ss_launch_count(self._h))
+
+    def profile_read(self, kind):
+        """(total_ms, flops, launches) of one kernel kind (needs profile=1)."""
+        ms, fl, n = C.c_double(), C.c_double(), C.c_longlong()
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        self._check(self._lib.ss_profile_read(self._h, k, C.byref(ms), C.byref(fl), C.byref(n)))
+        return ms.value, fl.value, n.value
+
+    def profile_reset(self):
+        self._check(self._lib.ss_profile_reset(self._h))
+
+    def _check(self, rc, allow=()):
+        if rc != SS_OK and rc not in allow:
+            raise SSError(rc, self.last_error())
+        return rc
+
+    # ------------------------------------------------------------------ calls
+    def set_hamiltonian(self, k_id, H_diag, H_up, S_diag, S_up, lead_L=None, lead_R=None):
+        """ss_set_hamiltonian; arrays (n_b,s,s), (n_b-1,s,s); leads (4,s,s) or None."""
+        n_b, s = int(H_diag.shape[0]), int(H_diag.shape[1])
+        if not self.device_ptrs:
+            H_diag, S_diag = _host_c128(H_diag), _host_c128(S_diag)
+            H_up, S_up = _host_c128(H_up), _host_c128(S_up)
+            lead_L = None if lead_L is None else _host_c128(lead_L)
+            lead_R = None if lead_R is None else _host_c128(lead_R)
+        rc = self._lib.ss_set_hamiltonian(self._h, int(k_id), n_b, s, _ptr(H_diag), _ptr(H_up), _ptr(S_diag),
+                                          _ptr(S_up), _ptr(lead_L), _ptr(lead_R))
+        self._check(rc)
+        self.shapes[int(k_id)] = (n_b, s)
+
+    def set_device(self, k_id, dev):
+        """set_hamiltonian from a ``synth.Device`` (numpy, host mode only)."""
+        lead = lambda t: None if t is None else np.stack(t)
+        self.set_hamiltonian(k_id, dev.H_diag, dev.H_up, dev.S_diag, dev.S_up, lead(dev.lead_L),
+                             lead(dev.lead_R))
+
+    def _pts(self, E, k_id):
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        k = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(k_id), E.shape), dtype=np.int32)
+        return E, k
+
+    def _alloc(self, count, dtype):
+        if self.device_ptrs:
+            import torch
+            tdt = torch.complex128 if dtype == np.complex128 else torch.float64
+            return torch.zeros(count, dtype=tdt, device="cuda")
+        return np.zeros(count, dtype)
+
+    def self_energy(self, E, k_id, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
+        """Returns (Sigma_L, Sigma_R, iters (P,2), status (P,), rc)."""
+        E, k = self._pts(E, k_id)
+        P = E.size
+        sizes = [self.shapes[int(q)][1] ** 2 for q in k]
+        tot = int(sum(sizes))
+        sL = self._alloc(tot, np.complex128)
+        sR = self._alloc(tot, np.complex128)
+        it = np.zeros(2 * P, np.int32)
+        st = np.zeros(P, np.int32)
+        rc = self._lib.ss_self_energy(self._h, P, E.ctypes.data_as(C.POINTER(C.c_double)),
+                                      k.ctypes.data_as(C.POINTER(C.c_int)), _ptr(sL), _ptr(sR),
+                                      it.ctypes.data_as(C.POINTER(C.c_int)), st.ctypes.data_as(C.POINTER(C.c_int)))
+        self._check(rc, allow)
+        return self._split(sL, k), self._split(sR, k), it.reshape(P, 2), st, rc
+
+    def _split(self, flat, k):
+        out, o = [], 0
+        for q in k:
+            s = self.shapes[int(q)][1]
+            out.append(flat[o:o + s * s].reshape(s, s))
+            o += s * s
+        return out
+
+    def solve(self, E, k_id, inj, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR), want_x=True):
+        """ss_solve; inj: list of (2s, n_inj) per point (or one packed array).
+
+        Returns (x list of (n_b*s, n_inj), status, rc)."""
+        E, k = self._pts(E, k_id)
+        P = E.size
+        if isinstance(inj, (list, tuple)):
+            n_inj = int(inj[0].shape[1])
+            if self.device_ptrs:
+                import torch
+                flat = torch.cat([t.reshape(-1) for t in inj])
+            else:
+                flat = np.concatenate([_host_c128(a).reshape(-1) for a in inj])
+        else:
+            n_inj = int(inj.shape[-1])
+            flat = inj.reshape(-1) if self.device_ptrs else _host_c128(inj).reshape(-1)
+        xs = sum(self.shapes[int(q)][0] * self.shapes[int(q)][1] for q in k) * n_inj
+        x = self._alloc(xs, np.complex128) if want_x else None
+        st = np.zeros(P, np.int32)
+        rc = self._lib.ss_solve(self._h, P, E.ctypes.data_as(C.POINTER(C.c_double)),
+                                k.ctypes.data_as(C.POINTER(C.c_int)), n_inj, _ptr(flat), _ptr(x),
+                                st.ctypes.data_as(C.POINTER(C.c_int)))
+        self._check(rc, allow)
+        out = None
+        if want_x:
+            out, o = [], 0
+            for q in k:
+                n, s = self.shapes[int(q)]
+                out.append(x[o:o + n * s * n_inj].reshape(n * s, n_inj))
+                o += n * s * n_inj
+        return out, st, rc
+
+    def transmission(self, E, k_id, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
+        """Returns (T (P,), err_est (P,), status (P,), rc)."""
+        E, k = self._pts(E, k_id)
+        P = E.size
+        T = self._alloc(P, np.float64)
+        err = self._alloc(P, np.float64)
+        st = np.zeros(P, np.int32)
+        rc = self._lib.ss_transmission(self._h, P, E.ctypes.data_as(C.POINTER(C.c_double)),
+                                       k.ctypes.data_as(C.POINTER(C.c_int)), _ptr(T), _ptr(err),
+                                       st.ctypes.data_as(C.POINTER(C.c_int)))
+        self._check(rc, allow)
+        return T, err, st, rc
+
+
+def ss_create(**kw) -> Handle:
+    return Handle(**kw)

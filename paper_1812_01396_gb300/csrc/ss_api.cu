@@ -1,0 +1,988 @@
+// C ABI and pipeline of the SplitSolve hot path (see include/splitsolve.h).
+//
+// Per batch ("chunk") of (E,k) points the pipeline is
+//   1. self-energies: Sancho-Rubio doubling on both leads of every point
+//      (2 problems per point), iterations replayed from a captured graph until
+//      every problem has converged or hit the cap (decimation, Sec. 3A);
+//   2. block sweeps: Algorithm 1 for the first block column and its mirror for
+//      the last one, both directions of every point in the same launches
+//      (Sec. 3B, "two accelerators" become two problem groups on one GPU);
+//   3. boundary correction of Eq. x: R = 1 - C Q, LU(R), z, x = Q (b' + z) and
+//      the corner G_1n of (A - B C)^-1;
+//   4. T = Re Tr[Gamma_L G_1n Gamma_R G_1n^H].
+// Points are ordered longest-first by n_b * s_b^3 and cut into chunks that
+// fit the workspace allocated at ss_create (the batch scheduler).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "splitsolve.h"
+#include "ss_internal.cuh"
+#include "ss_plan.h"
+
+using namespace ss;
+
+namespace {
+
+constexpr int LU_NB = 32;
+constexpr int MAX_K_ID = 4096;
+
+std::string g_create_error;
+
+struct KData {
+  int n = 0, s = 0;
+  z64 *Hd = nullptr, *Hu = nullptr, *Sd = nullptr, *Su = nullptr, *lead = nullptr;
+  // lead cells: [side][0..3] = H00, H01, S00, S01
+  const z64* cell[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+  void free_all() {
+    cudaFree(Hd); cudaFree(Hu); cudaFree(Sd); cudaFree(Su); cudaFree(lead);
+    Hd = Hu = Sd = Su = lead = nullptr;
+  }
+};
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Workspace of one point inside a chunk.
+struct PW {
+  int idx = 0;  // position in the call's arrays
+  int n = 0, s = 0;
+  double E = 0.0;
+  const KData* kd = nullptr;
+  // self-energy doubling, side 0 = left lead, 1 = right lead
+  z64 *D[2], *e[2], *es[2], *a[2][2], *b[2][2], *T1[2], *T2[2], *Wd[2];
+  int* ipd[2];
+  z64* sig[2];
+  // sweeps, dir 0 = first block column, 1 = last block column
+  z64 *X[2], *Ws[2], *tmp[2];
+  int* ips[2];
+  // boundary
+  z64 *Rw, *gb, *cv, *G1n, *Gam[2], *M1, *M2;
+  int* ipr;
+  z64* inj;  // device copy or user pointer (2s x ninj)
+  z64* x;    // device output (N x ninj)
+};
+
+size_t point_bytes(int n, int s, int ninj) {
+  Carve c(nullptr);
+  const size_t ss2 = (size_t)s * s;
+  for (int q = 0; q < 2; ++q) {
+    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
+    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
+    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(3 * ss2); c.take<int>(s);
+    c.take<z64>(ss2);
+    c.take<z64>((size_t)n * ss2); c.take<z64>(2 * ss2); c.take<z64>(ss2); c.take<int>(s);
+  }
+  c.take<z64>((size_t)2 * s * (3 * s + ninj)); c.take<z64>((size_t)2 * s * ninj);
+  c.take<z64>((size_t)2 * s * ninj); c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
+  c.take<z64>(ss2); c.take<z64>(ss2); c.take<int>(2 * s);
+  c.take<z64>((size_t)2 * s * ninj);          // injection staging
+  c.take<z64>((size_t)n * s * ninj);          // x staging
+  return c.off + 256;
+}
+
+void carve_point(Carve& c, PW& w, int ninj) {
+  const int n = w.n, s = w.s;
+  const size_t ss2 = (size_t)s * s;
+  for (int q = 0; q < 2; ++q) {
+    w.D[q] = c.take<z64>(ss2); w.e[q] = c.take<z64>(ss2); w.es[q] = c.take<z64>(ss2);
+    w.a[q][0] = c.take<z64>(ss2); w.a[q][1] = c.take<z64>(ss2);
+    w.b[q][0] = c.take<z64>(ss2); w.b[q][1] = c.take<z64>(ss2);
+    w.T1[q] = c.take<z64>(ss2); w.T2[q] = c.take<z64>(ss2); w.Wd[q] = c.take<z64>(3 * ss2);
+    w.ipd[q] = c.take<int>(s);
+    w.sig[q] = c.take<z64>(ss2);
+    w.X[q] = c.take<z64>((size_t)n * ss2); w.Ws[q] = c.take<z64>(2 * ss2); w.tmp[q] = c.take<z64>(ss2);
+    w.ips[q] = c.take<int>(s);
+  }
+  w.Rw = c.take<z64>((size_t)2 * s * (3 * s + ninj)); w.gb = c.take<z64>((size_t)2 * s * ninj);
+  w.cv = c.take<z64>((size_t)2 * s * ninj); w.G1n = c.take<z64>(ss2);
+  w.Gam[0] = c.take<z64>(ss2); w.Gam[1] = c.take<z64>(ss2); w.M1 = c.take<z64>(ss2); w.M2 = c.take<z64>(ss2);
+  w.ipr = c.take<int>(2 * s);
+  w.inj = c.take<z64>((size_t)2 * s * ninj);
+  w.x = c.take<z64>((size_t)n * s * ninj);
+}
+
+// ------------------------------------------------------------ descriptors
+Operand plain(const z64* p, int ld, int trans = 0) {
+  Operand o{};
+  o.p = p; o.s = nullptr; o.e = make_double2(0.0, 0.0); o.ld = ld; o.trans = trans;
+  return o;
+}
+Operand formed(const z64* S, const z64* H, z64 e, int ld, int trans = 0) {
+  Operand o{};
+  o.p = H; o.s = S; o.e = e; o.ld = ld; o.trans = trans;
+  return o;
+}
+GemmDesc gdesc(int m, int n, int k, Operand a, Operand b, z64* c, int ldc, z64 alpha, z64 beta,
+               const int* active = nullptr) {
+  GemmDesc g{};
+  g.m = m; g.n = n; g.k = k; g.a = a; g.b = b; g.c = c; g.ldc = ldc; g.cmode = 0;
+  g.alpha = alpha; g.beta = beta; g.active = active;
+  return g;
+}
+FormDesc fdesc(z64* out, int ldo, int rows, int cols) {
+  FormDesc f{};
+  f.out = out; f.ldo = ldo; f.rows = rows; f.cols = cols;
+  f.ax = f.ay = f.az = f.gamma = make_double2(0.0, 0.0);
+  return f;
+}
+FormDesc fcopy(z64* out, int ldo, const z64* in, int ldi, int rows, int cols, int trans = 0) {
+  FormDesc f = fdesc(out, ldo, rows, cols);
+  f.x = in; f.ldx = ldi; f.tx = trans; f.ax = make_double2(1.0, 0.0);
+  return f;
+}
+// out = e * op(S) - op(H)
+FormDesc fformed(z64* out, int ldo, const z64* S, const z64* H, z64 e, int ld, int rows, int cols,
+                 int trans = 0) {
+  FormDesc f = fdesc(out, ldo, rows, cols);
+  f.x = S; f.ldx = ld; f.tx = trans; f.ax = e;
+  f.y = H; f.ldy = ld; f.ty = trans; f.ay = make_double2(-1.0, 0.0);
+  return f;
+}
+FormDesc fident(z64* out, int ldo, int rows, int cols, double g) {
+  FormDesc f = fdesc(out, ldo, rows, cols);
+  f.gamma = make_double2(g, 0.0);
+  return f;
+}
+
+const z64 ONE = {1.0, 0.0}, ZERO = {0.0, 0.0}, MONE = {-1.0, 0.0};
+
+}  // namespace
+
+// --------------------------------------------------------------- the handle
+struct ss_handle {
+  ss_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::map<int, KData> ks;
+  std::string err;
+  long long nlaunch = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // per-chunk device scalars
+  int* dint = nullptr;      // flags, iterations, infos
+  double* ddbl = nullptr;   // norms
+  z64* dtr = nullptr;       // traces
+  size_t dint_n = 0, ddbl_n = 0, dtr_n = 0;
+  Plan p_setup, p_iter[2], p_final, p_sweep, p_bound;
+  Prof prof;
+  Prof* P() { return cfg.profile ? &prof : nullptr; }
+  // cache of the last chunk
+  std::vector<double> cE;
+  std::vector<int> cK;
+  bool c_sigma = false, c_T = false;
+  std::vector<double> cT, cTi;
+  std::vector<int> c_iters, c_status;
+};
+
+namespace {
+
+int fail(ss_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+int cuda_fail(ss_handle* h, cudaError_t e, const char* where) {
+  return fail(h, SS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call, where)                              \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
+  } while (0)
+
+// ---------------------------------------------------------- self-energies
+// Builds setup / iteration / final plans for the doubling of 2P lead problems.
+void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, int* conv,
+                      int* info, double* na, double* nb, double* nd) {
+  const int P = (int)pts.size();
+  const int NP = 2 * P;
+  const double eta = h->cfg.eta;
+  Plan& S = h->p_setup;
+  S.clear();
+  std::vector<FormDesc> f;
+  std::vector<Norm1Desc> nD, nA;
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const int s = w.s;
+    const z64 z = make_double2(w.E, eta);
+    for (int q = 0; q < 2; ++q) {
+      const z64* const* c = w.kd->cell[q];
+      f.push_back(fformed(w.D[q], s, c[2], c[0], z, s, s, s));
+      f.push_back(fformed(w.e[q], s, c[2], c[0], z, s, s, s));
+      f.push_back(fformed(w.es[q], s, c[2], c[0], z, s, s, s));
+      f.push_back(fformed(w.a[q][0], s, c[3], c[1], z, s, s, s));
+      // L = z S01^H - H01^H
+      f.push_back(fformed(w.b[q][0], s, c[3], c[1], z, s, s, s, 1));
+    }
+  }
+  S.form(f);
+  S.memset0(na, sizeof(double) * NP);
+  S.memset0(nb, sizeof(double) * NP);
+  S.memset0(nd, sizeof(double) * NP);
+  S.fill(act, NP, 1);
+  S.memset0(iters, sizeof(int) * NP);
+  S.memset0(conv, sizeof(int) * NP);
+  S.memset0(info, sizeof(int) * NP * 2);
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    for (int q = 0; q < 2; ++q) {
+      const int i = 2 * p + q;
+      nD.push_back({w.D[q], w.s, w.s, w.s, nd + i, nullptr});
+      nA.push_back({w.a[q][0], w.s, w.s, w.s, na + i, nullptr});
+      nA.push_back({w.b[q][0], w.s, w.s, w.s, nb + i, nullptr});
+    }
+  }
+  S.norm1(nD);
+  S.norm1(nA);
+  S.check(na, nb, nd, act, iters, conv, NP, h->cfg.decim_tol, h->cfg.decim_max_iter, 0);
+
+  for (int ping = 0; ping < 2; ++ping) {
+    Plan& I = h->p_iter[ping];
+    I.clear();
+    const int pong = 1 - ping;
+    std::vector<FormDesc> f1, f2;
+    std::vector<LuDesc> lu;
+    std::vector<GemmDesc> g;
+    std::vector<Norm1Desc> nr;
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const int s = w.s, ld = 3 * s;
+      for (int q = 0; q < 2; ++q) {
+        const int i = 2 * p + q;
+        const int* ac = act + i;
+        z64* W = w.Wd[q];
+        FormDesc x;
+        x = fcopy(W, ld, w.e[q], s, s, s); x.active = ac; f1.push_back(x);
+        x = fcopy(W + s, ld, w.a[q][ping], s, s, s); x.active = ac; f1.push_back(x);
+        x = fcopy(W + 2 * s, ld, w.b[q][ping], s, s, s); x.active = ac; f1.push_back(x);
+        LuDesc L{};
+        L.w = W; L.ldw = ld; L.s = s; L.ncols = 3 * s; L.ipiv = w.ipd[q]; L.info = info + i;
+        L.active = ac;
+        lu.push_back(L);
+        const z64* ga = W + s;
+        const z64* gbp = W + 2 * s;
+        g.push_back(gdesc(s, s, s, plain(w.a[q][ping], s), plain(gbp, ld), w.T1[q], s, ONE, ZERO, ac));
+        g.push_back(gdesc(s, s, s, plain(w.b[q][ping], s), plain(ga, ld), w.T2[q], s, ONE, ZERO, ac));
+        g.push_back(gdesc(s, s, s, plain(w.a[q][ping], s), plain(ga, ld), w.a[q][pong], s, MONE, ZERO, ac));
+        g.push_back(gdesc(s, s, s, plain(w.b[q][ping], s), plain(gbp, ld), w.b[q][pong], s, MONE, ZERO, ac));
+        // e -= T1 + T2 ; es_R -= T1 (right lead) or es_L -= T2 (left lead)
+        FormDesc u = fcopy(w.e[q], s, w.e[q], s, s, s);
+        u.y = w.T1[q]; u.ldy = s; u.ay = MONE;
+        u.z = w.T2[q]; u.ldz = s; u.az = MONE;
+        u.active = ac;
+        f2.push_back(u);
+        FormDesc v = fcopy(w.es[q], s, w.es[q], s, s, s);
+        v.y = (q == 1) ? w.T1[q] : w.T2[q]; v.ldy = s; v.ay = MONE;
+        v.active = ac;
+        f2.push_back(v);
+        nr.push_back({w.a[q][pong], s, s, s, na + i, ac});
+        nr.push_back({w.b[q][pong], s, s, s, nb + i, ac});
+      }
+    }
+    I.form(f1);
+    I.lu_solve(lu, LU_NB);
+    I.gemm(g);
+    I.form(f2);
+    I.norm1(nr);
+    I.check(na, nb, nd, act, iters, conv, NP, h->cfg.decim_tol, h->cfg.decim_max_iter, 1);
+  }
+
+  // Sigma_L = A_{1,0} es_L^-1 A_{0,1};  Sigma_R = A_{n,n+1} es_R^-1 A_{n+1,n}
+  Plan& F = h->p_final;
+  F.clear();
+  std::vector<FormDesc> ff;
+  std::vector<LuDesc> lu;
+  std::vector<GemmDesc> g;
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const int s = w.s, ld = 3 * s;
+    const z64 E = make_double2(w.E, 0.0);
+    for (int q = 0; q < 2; ++q) {
+      const z64* const* c = w.kd->cell[q];
+      z64* W = w.Wd[q];
+      ff.push_back(fcopy(W, ld, w.es[q], s, s, s));
+      // right: rhs A_{n+1,n} = (E S01 - H01)^H ; left: rhs A_{0,1} = E S01 - H01
+      ff.push_back(fformed(W + s, ld, c[3], c[1], E, s, s, s, q == 1 ? 1 : 0));
+      LuDesc L{};
+      L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[q]; L.info = info + NP + 2 * p + q;
+      lu.push_back(L);
+      g.push_back(gdesc(s, s, s, formed(c[3], c[1], E, s, q == 1 ? 0 : 1), plain(W + s, ld), w.sig[q], s,
+                        ONE, ZERO));
+    }
+  }
+  F.form(ff);
+  F.lu_solve(lu, LU_NB);
+  F.gemm(g);
+}
+
+// ------------------------------------------------------------------ sweeps
+void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
+  Plan& S = h->p_sweep;
+  S.clear();
+  const int P = (int)pts.size();
+  S.memset0(info, sizeof(int) * 2 * P * nmax);
+  for (int t = 0; t < nmax; ++t) {
+    std::vector<GemmDesc> g;
+    std::vector<FormDesc> f, fc;
+    std::vector<LuDesc> lu;
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const int n = w.n, s = w.s, ld = 2 * s;
+      if (t >= n) continue;
+      const KData* kd = w.kd;
+      const size_t ss2 = (size_t)s * s;
+      const z64 E = make_double2(w.E, 0.0);
+      for (int dir = 0; dir < 2; ++dir) {
+        const int i = dir == 0 ? n - t : t + 1;  // 1-based block
+        z64* W = w.Ws[dir];
+        const z64* Sii = kd->Sd + (i - 1) * ss2;
+        const z64* Hii = kd->Hd + (i - 1) * ss2;
+        if (t == 0) {
+          f.push_back(fformed(W, ld, Sii, Hii, E, s, s, s));
+        } else {
+          // D_i = A_ii - A_{i,i+1} X_{i+1} (first) or A_ii - A_{i,i-1} Y_{i-1} (last)
+          const int up = dir == 0 ? i - 1 : i - 2;  // 0-based upper block index
+          const int prev = dir == 0 ? i + 1 : i - 1;
+          GemmDesc q = gdesc(s, s, s, formed(kd->Su + up * ss2, kd->Hu + up * ss2, E, s, dir == 0 ? 0 : 1),
+                             plain(w.X[dir] + (prev - 1) * ss2, s), W, ld, MONE, ONE);
+          q.cmode = 1; q.cs = Sii; q.ch = Hii; q.ce = E; q.ldcf = s;
+          g.push_back(q);
+        }
+        // right-hand side: A_{i,i-1} (first, I at i = 1) / A_{i,i+1} (last, I at i = n)
+        if (dir == 0) {
+          if (i > 1) f.push_back(fformed(W + s, ld, kd->Su + (i - 2) * ss2, kd->Hu + (i - 2) * ss2, E, s, s, s, 1));
+          else f.push_back(fident(W + s, ld, s, s, 1.0));
+        } else {
+          if (i < n) f.push_back(fformed(W + s, ld, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s, 0));
+          else f.push_back(fident(W + s, ld, s, s, 1.0));
+        }
+        LuDesc L{};
+        L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ips[dir];
+        L.info = info + (size_t)(2 * p + dir) * nmax + t;
+        lu.push_back(L);
+        fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, W + s, ld, s, s));
+      }
+    }
+    S.gemm(g);
+    S.form(f);
+    S.lu_solve(lu, LU_NB);
+    S.form(fc);
+  }
+  // chains: Q_i = -X_i Q_{i-1} (first), P_i = -Y_i P_{i+1} (last)
+  for (int t = 1; t < nmax; ++t) {
+    std::vector<GemmDesc> g;
+    std::vector<FormDesc> fc;
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const int n = w.n, s = w.s;
+      if (t >= n) continue;
+      const size_t ss2 = (size_t)s * s;
+      for (int dir = 0; dir < 2; ++dir) {
+        const int i = dir == 0 ? t + 1 : n - t;
+        const int prev = dir == 0 ? i - 1 : i + 1;
+        g.push_back(gdesc(s, s, s, plain(w.X[dir] + (i - 1) * ss2, s), plain(w.X[dir] + (prev - 1) * ss2, s),
+                          w.tmp[dir], s, MONE, ZERO));
+        fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, w.tmp[dir], s, s, s));
+      }
+    }
+    S.gemm(g);
+    S.form(fc);
+  }
+}
+
+// ---------------------------------------------------------------- boundary
+void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64* traces) {
+  Plan& B = h->p_bound;
+  B.clear();
+  const int P = (int)pts.size();
+  B.memset0(info, sizeof(int) * P);
+  std::vector<FormDesc> f0, fc, fg;
+  std::vector<GemmDesc> gR, gb1, gb2, gsb, gG1, gG2, gx1, gx2, gM;
+  std::vector<LuDesc> lu;
+  std::vector<TraceDesc> tr;
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const int n = w.n, s = w.s, ld = 3 * s + ninj;
+    const size_t ss2 = (size_t)s * s;
+    const z64* G11 = w.X[0];
+    const z64* Gn1 = w.X[0] + (size_t)(n - 1) * ss2;
+    const z64* G1n = w.X[1];
+    const z64* Gnn = w.X[1] + (size_t)(n - 1) * ss2;
+    z64* R = w.Rw;
+    f0.push_back(fident(R + 2 * s, ld, s, s, 0.0));
+    f0.push_back(fident(R + (size_t)s * ld + 2 * s, ld, s, s, 1.0));
+    GemmDesc q;
+    q = gdesc(s, s, s, plain(w.sig[0], s), plain(G11, s), R, ld, MONE, ONE); q.cmode = 2; gR.push_back(q);
+    gR.push_back(gdesc(s, s, s, plain(w.sig[0], s), plain(G1n, s), R + s, ld, MONE, ZERO));
+    gR.push_back(gdesc(s, s, s, plain(w.sig[1], s), plain(Gn1, s), R + (size_t)s * ld, ld, MONE, ZERO));
+    q = gdesc(s, s, s, plain(w.sig[1], s), plain(Gnn, s), R + (size_t)s * ld + s, ld, MONE, ONE); q.cmode = 2;
+    gR.push_back(q);
+    if (ninj > 0) {
+      const z64* b1 = w.inj;
+      const z64* bn = w.inj + (size_t)s * ninj;
+      gb1.push_back(gdesc(s, ninj, s, plain(G11, s), plain(b1, ninj), w.gb, ninj, ONE, ZERO));
+      gb1.push_back(gdesc(s, ninj, s, plain(Gn1, s), plain(b1, ninj), w.gb + (size_t)s * ninj, ninj, ONE, ZERO));
+      gb2.push_back(gdesc(s, ninj, s, plain(G1n, s), plain(bn, ninj), w.gb, ninj, ONE, ONE));
+      gb2.push_back(gdesc(s, ninj, s, plain(Gnn, s), plain(bn, ninj), w.gb + (size_t)s * ninj, ninj, ONE, ONE));
+      gsb.push_back(gdesc(s, ninj, s, plain(w.sig[0], s), plain(w.gb, ninj), R + 3 * s, ld, ONE, ZERO));
+      gsb.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.gb + (size_t)s * ninj, ninj),
+                          R + (size_t)s * ld + 3 * s, ld, ONE, ZERO));
+      // c = b' + z
+      FormDesc c1 = fcopy(w.cv, ninj, b1, ninj, s, ninj);
+      c1.y = R + 3 * s; c1.ldy = ld; c1.ay = ONE;
+      fc.push_back(c1);
+      FormDesc c2 = fcopy(w.cv + (size_t)s * ninj, ninj, bn, ninj, s, ninj);
+      c2.y = R + (size_t)s * ld + 3 * s; c2.ldy = ld; c2.ay = ONE;
+      fc.push_back(c2);
+      for (int i = 0; i < n; ++i) {
+        z64* xi = w.x + (size_t)i * s * ninj;
+        gx1.push_back(gdesc(s, ninj, s, plain(w.X[0] + i * ss2, s), plain(w.cv, ninj), xi, ninj, ONE, ZERO));
+        gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.cv + (size_t)s * ninj, ninj), xi,
+                            ninj, ONE, ONE));
+      }
+    }
+    LuDesc L{};
+    L.w = R; L.ldw = ld; L.s = 2 * s; L.ncols = ld; L.ipiv = w.ipr; L.info = info + p;
+    lu.push_back(L);
+    // G_1n of the open system = G11 w_top + G1n w_bot, w = R^-1 [0; 1]
+    gG1.push_back(gdesc(s, s, s, plain(G11, s), plain(R + 2 * s, ld), w.G1n, s, ONE, ZERO));
+    gG2.push_back(gdesc(s, s, s, plain(G1n, s), plain(R + (size_t)s * ld + 2 * s, ld), w.G1n, s, ONE, ONE));
+    // Gamma = i Sigma - i Sigma^H
+    for (int q2 = 0; q2 < 2; ++q2) {
+      FormDesc gm = fdesc(w.Gam[q2], s, s, s);
+      gm.x = w.sig[q2]; gm.ldx = s; gm.ax = make_double2(0.0, 1.0);
+      gm.y = w.sig[q2]; gm.ldy = s; gm.ty = 1; gm.ay = make_double2(0.0, -1.0);
+      fg.push_back(gm);
+    }
+    gM.push_back(gdesc(s, s, s, plain(w.Gam[0], s), plain(w.G1n, s), w.M1, s, ONE, ZERO));
+    gM.push_back(gdesc(s, s, s, plain(w.Gam[1], s), plain(w.G1n, s, 1), w.M2, s, ONE, ZERO));
+    tr.push_back({w.M1, s, w.M2, s, s, traces + p, nullptr});
+  }
+  B.form(f0);
+  B.gemm(gR);
+  B.gemm(gb1);
+  B.gemm(gb2);
+  B.gemm(gsb);
+  B.lu_solve(lu, LU_NB);
+  B.gemm(gG1);
+  B.gemm(gG2);
+  B.form(fc);
+  B.gemm(gx1);
+  B.gemm(gx2);
+  B.form(fg);
+  B.gemm(gM);
+  B.trace(tr);
+}
+
+bool same_points(const ss_handle* h, int n, const double* E, const int* k) {
+  if ((int)h->cE.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (h->cE[i] != E[i] || h->cK[i] != k[i]) return false;
+  return true;
+}
+
+int ensure_scalars(ss_handle* h, size_t ni, size_t nd, size_t nt) {
+  if (ni > h->dint_n) {
+    cudaFree(h->dint); h->dint = nullptr; h->dint_n = 0;
+    CK(cudaMalloc(&h->dint, ni * sizeof(int)), "cudaMalloc(flags)");
+    h->dint_n = ni;
+  }
+  if (nd > h->ddbl_n) {
+    cudaFree(h->ddbl); h->ddbl = nullptr; h->ddbl_n = 0;
+    CK(cudaMalloc(&h->ddbl, nd * sizeof(double)), "cudaMalloc(norms)");
+    h->ddbl_n = nd;
+  }
+  if (nt > h->dtr_n) {
+    cudaFree(h->dtr); h->dtr = nullptr; h->dtr_n = 0;
+    CK(cudaMalloc(&h->dtr, nt * sizeof(z64)), "cudaMalloc(traces)");
+    h->dtr_n = nt;
+  }
+  return SS_OK;
+}
+
+// What a pipeline call must produce.
+struct Want {
+  bool sigma_out = false;
+  bool solve = false;   // sweeps + boundary + trace
+  int ninj = 0;
+  const ss_c64* inj = nullptr;
+  ss_c64* x = nullptr;
+  ss_c64* sigL = nullptr;
+  ss_c64* sigR = nullptr;
+};
+
+int worst(int a, int b) { return a != SS_OK ? a : b; }
+
+// Run the pipeline over the points of one call (chunked).
+int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const Want& want,
+               std::vector<int>& status, std::vector<int>& iters, std::vector<double>& T,
+               std::vector<double>& Ti) {
+  if (n_pts < 0) return fail(h, SS_ERR_ARG, "n_pts < 0");
+  if (n_pts == 0) return SS_OK;
+  if (!E || !k_id) return fail(h, SS_ERR_ARG, "E and k_id must be non-NULL");
+  if (want.ninj < 0 || want.ninj > h->cfg.max_inj) return fail(h, SS_ERR_ARG, "n_inj outside 1..max_inj");
+  status.assign(n_pts, SS_OK);
+  iters.assign(2 * n_pts, 0);
+  T.assign(n_pts, 0.0);
+  Ti.assign(n_pts, 0.0);
+  // offsets of per-point packed arrays
+  std::vector<size_t> off_ss(n_pts), off_inj(n_pts), off_x(n_pts);
+  size_t a_ss = 0, a_inj = 0, a_x = 0;
+  std::vector<int> order(n_pts);
+  for (int i = 0; i < n_pts; ++i) {
+    auto it = h->ks.find(k_id[i]);
+    if (it == h->ks.end()) return fail(h, SS_ERR_STATE, "no Hamiltonian set for k_id " + std::to_string(k_id[i]));
+    if (!std::isfinite(E[i])) return fail(h, SS_ERR_ARG, "non-finite energy");
+    const int s = it->second.s, n = it->second.n;
+    off_ss[i] = a_ss; a_ss += (size_t)s * s;
+    off_inj[i] = a_inj; a_inj += (size_t)2 * s * want.ninj;
+    off_x[i] = a_x; a_x += (size_t)n * s * want.ninj;
+    order[i] = i;
+  }
+  // longest-processing-time first
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const KData& ka = h->ks[k_id[a]];
+    const KData& kb = h->ks[k_id[b]];
+    return (double)ka.n * ka.s * ka.s * ka.s > (double)kb.n * kb.s * kb.s * kb.s;
+  });
+  // reuse of the previous call's self-energies when the point list is identical
+  const bool reuse_sigma = h->c_sigma && same_points(h, n_pts, E, k_id) && n_pts <= h->cfg.max_points;
+  const bool dp = h->cfg.device_ptrs != 0;
+  cudaStream_t st = h->stream;
+  int rc_all = SS_OK;
+
+  size_t pos = 0;
+  while (pos < (size_t)n_pts) {
+    // chunk: as many points as fit the arena and max_points
+    std::vector<PW> pts;
+    size_t bytes = 0;
+    while (pos < (size_t)n_pts && (int)pts.size() < h->cfg.max_points) {
+      const int i = order[pos];
+      const KData& kd = h->ks[k_id[i]];
+      const size_t need = point_bytes(kd.n, kd.s, h->cfg.max_inj);
+      if (!pts.empty() && bytes + need > h->arena_bytes) break;
+      if (need > h->arena_bytes) return fail(h, SS_ERR_OOM, "one point does not fit the workspace");
+      bytes += need;
+      PW w;
+      w.idx = i; w.n = kd.n; w.s = kd.s; w.E = E[i]; w.kd = &kd;
+      pts.push_back(w);
+      ++pos;
+    }
+    const int P = (int)pts.size();
+    // the layout depends only on (n, s) and max_inj, so cached self-energies
+    // stay at the same addresses whatever n_inj the next call uses
+    Carve c(h->arena);
+    int nmax = 0;
+    for (auto& w : pts) { carve_point(c, w, h->cfg.max_inj); nmax = std::max(nmax, w.n); }
+    // device scalars: act, iters, conv (2P each), decim info (4P), sweep info (2P*nmax), bound info (P)
+    const size_t ni = 2 * P * 3 + 4 * P + 2 * (size_t)P * nmax + P;
+    int rc = ensure_scalars(h, ni, 3 * 2 * P, P);
+    if (rc) return rc;
+    int* act = h->dint;
+    int* itr = act + 2 * P;
+    int* conv = itr + 2 * P;
+    int* dinfo = conv + 2 * P;
+    int* sinfo = dinfo + 4 * P;
+    int* binfo = sinfo + 2 * (size_t)P * nmax;
+    double* na = h->ddbl;
+    double* nb = na + 2 * P;
+    double* nd = nb + 2 * P;
+
+    // inputs
+    if (want.solve && want.ninj > 0) {
+      for (auto& w : pts) {
+        const size_t cnt = (size_t)2 * w.s * want.ninj;
+        const ss_c64* src = want.inj + off_inj[w.idx];
+        if (dp) CK(cudaMemcpyAsync(w.inj, src, cnt * sizeof(z64), cudaMemcpyDeviceToDevice, st), "copy inj");
+        else CK(cudaMemcpyAsync(w.inj, src, cnt * sizeof(z64), cudaMemcpyHostToDevice, st), "copy inj");
+        if (dp && want.x) w.x = reinterpret_cast<z64*>(want.x + off_x[w.idx]);
+      }
+    }
+
+    // 1. self-energies
+    std::vector<int> h_it(2 * P, 0), h_conv(2 * P, 1), h_dinfo(4 * P, 0);
+    if (!reuse_sigma) {
+      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd);
+      CK(h->p_setup.upload(st), "upload setup");
+      CK(h->p_iter[0].upload(st), "upload iter");
+      CK(h->p_iter[1].upload(st), "upload iter");
+      CK(h->p_final.upload(st), "upload final");
+      CK(h->p_setup.run(st, &h->nlaunch, h->P()), "decimation setup");
+      std::vector<int> h_act(2 * P, 1);
+      const int cap = h->cfg.decim_max_iter;
+      if (h->cfg.profile) {
+        // one step at a time so the flop count sees exactly the active problems
+        h->prof.act_dev = act;
+        h->prof.act_host = h_act.data();
+        h->prof.nact = 2 * P;
+        CK(cudaMemcpyAsync(h_act.data(), act, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read flags");
+        CK(cudaStreamSynchronize(st), "doubling sync");
+        for (int it = 0; it < cap + 1; ++it) {
+          bool any = false;
+          for (int v : h_act) any = any || v;
+          if (!any) break;
+          CK(h->p_iter[it & 1].run(st, &h->nlaunch, &h->prof), "doubling step");
+          CK(cudaMemcpyAsync(h_act.data(), act, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read flags");
+          CK(cudaStreamSynchronize(st), "doubling sync");
+        }
+        h->prof.act_host = nullptr;
+        h->prof.collect();
+      } else {
+        for (int it = 0; it < cap + 2; it += 2) {
+          if (h->cfg.use_graphs) {
+            CK(h->p_iter[0].replay(st, &h->nlaunch), "doubling step");
+            CK(h->p_iter[1].replay(st, &h->nlaunch), "doubling step");
+          } else {
+            CK(h->p_iter[0].run(st, &h->nlaunch), "doubling step");
+            CK(h->p_iter[1].run(st, &h->nlaunch), "doubling step");
+          }
+          CK(cudaMemcpyAsync(h_act.data(), act, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read flags");
+          CK(cudaStreamSynchronize(st), "doubling sync");
+          bool any = false;
+          for (int v : h_act) any = any || v;
+          if (!any) break;
+        }
+      }
+      CK(h->p_final.run(st, &h->nlaunch, h->P()), "self-energy");
+      CK(cudaMemcpyAsync(h_it.data(), itr, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read iters");
+      CK(cudaMemcpyAsync(h_conv.data(), conv, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read conv");
+      CK(cudaMemcpyAsync(h_dinfo.data(), dinfo, sizeof(int) * 4 * P, cudaMemcpyDeviceToHost, st), "read info");
+    } else {
+      for (int p = 0; p < P; ++p) {
+        h_it[2 * p] = h->c_iters[2 * pts[p].idx];
+        h_it[2 * p + 1] = h->c_iters[2 * pts[p].idx + 1];
+      }
+    }
+    if (want.sigma_out) {
+      for (auto& w : pts) {
+        const size_t cnt = (size_t)w.s * w.s * sizeof(z64);
+        const cudaMemcpyKind kind = dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (want.sigL) CK(cudaMemcpyAsync(want.sigL + off_ss[w.idx], w.sig[0], cnt, kind, st), "copy sigma");
+        if (want.sigR) CK(cudaMemcpyAsync(want.sigR + off_ss[w.idx], w.sig[1], cnt, kind, st), "copy sigma");
+      }
+    }
+
+    // 2.-4. sweeps, boundary, transmission
+    std::vector<int> h_sinfo, h_binfo(P, 0);
+    std::vector<z64> h_tr(P);
+    if (want.solve) {
+      build_sweeps(h, pts, sinfo, nmax);
+      build_boundary(h, pts, want.x ? want.ninj : 0, binfo, h->dtr);
+      CK(h->p_sweep.upload(st), "upload sweeps");
+      CK(h->p_bound.upload(st), "upload boundary");
+      CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
+      CK(h->p_bound.run(st, &h->nlaunch, h->P()), "boundary");
+      h_sinfo.assign(2 * (size_t)P * nmax, 0);
+      CK(cudaMemcpyAsync(h_sinfo.data(), sinfo, sizeof(int) * h_sinfo.size(), cudaMemcpyDeviceToHost, st), "info");
+      CK(cudaMemcpyAsync(h_binfo.data(), binfo, sizeof(int) * P, cudaMemcpyDeviceToHost, st), "info");
+      CK(cudaMemcpyAsync(h_tr.data(), h->dtr, sizeof(z64) * P, cudaMemcpyDeviceToHost, st), "read T");
+      if (want.x && !dp) {
+        for (auto& w : pts) {
+          const size_t cnt = (size_t)w.n * w.s * want.ninj * sizeof(z64);
+          CK(cudaMemcpyAsync(want.x + off_x[w.idx], w.x, cnt, cudaMemcpyDeviceToHost, st), "copy x");
+        }
+      }
+    }
+    CK(cudaStreamSynchronize(st), "pipeline sync");
+    CK(cudaGetLastError(), "pipeline");
+    if (h->cfg.profile) h->prof.collect();
+
+    for (int p = 0; p < P; ++p) {
+      const int i = pts[p].idx;
+      iters[2 * i] = h_it[2 * p];
+      iters[2 * i + 1] = h_it[2 * p + 1];
+      int stt = SS_OK;
+      if (!reuse_sigma) {
+        if (!h_conv[2 * p] || !h_conv[2 * p + 1]) stt = SS_ERR_NOT_CONVERGED;
+        for (int q = 0; q < 4; ++q)
+          if (h_dinfo[(q < 2 ? 2 * p + q : 2 * P + 2 * p + q - 2)] && stt == SS_OK) stt = SS_ERR_SINGULAR;
+      }
+      if (want.solve) {
+        for (int d = 0; d < 2 && stt == SS_OK; ++d)
+          for (int t = 0; t < nmax; ++t)
+            if (h_sinfo[(size_t)(2 * p + d) * nmax + t]) {
+              stt = SS_ERR_SINGULAR;
+              if (h->err.empty())
+                h->err = "singular diagonal block in the sweep of point " + std::to_string(i);
+              break;
+            }
+        if (h_binfo[p] && stt == SS_OK) stt = SS_ERR_SINGULAR;
+        if (stt == SS_OK && !(std::isfinite(h_tr[p].x) && std::isfinite(h_tr[p].y))) {
+          stt = SS_ERR_SINGULAR;
+          h->err = "non-finite transmission at point " + std::to_string(i);
+        }
+        T[i] = h_tr[p].x;
+        Ti[i] = h_tr[p].y;
+      }
+      status[i] = stt;
+      rc_all = worst(rc_all, stt);
+    }
+  }
+  // cache
+  h->cE.assign(E, E + n_pts);
+  h->cK.assign(k_id, k_id + n_pts);
+  h->c_sigma = n_pts <= h->cfg.max_points;
+  h->c_iters = iters;
+  h->c_T = want.solve && n_pts <= h->cfg.max_points;
+  h->cT = T;
+  h->cTi = Ti;
+  h->c_status = status;
+  return rc_all;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+void ss_config_default(ss_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n_b_max = 64;
+  cfg->s_b_max = 512;
+  cfg->max_points = 8;
+  cfg->max_inj = 64;
+  cfg->precision = SS_FP64;
+  cfg->eta = 1e-10;
+  cfg->decim_tol = 1e-14;
+  cfg->decim_max_iter = 100;
+  cfg->ir_tol = 1e-14;
+  cfg->ir_max_iter = 10;
+  cfg->warm_start = 0;
+  cfg->stream = nullptr;
+  cfg->device_ptrs = 0;
+  cfg->use_graphs = 1;
+  cfg->profile = 0;
+}
+
+int ss_create(ss_handle** hp, const ss_config* cfg) {
+  if (!hp) { g_create_error = "NULL handle pointer"; return SS_ERR_ARG; }
+  *hp = nullptr;
+  if (!cfg) { g_create_error = "NULL config"; return SS_ERR_ARG; }
+  if (cfg->n_b_max < 1 || cfg->s_b_max < 1 || cfg->max_points < 1 || cfg->max_inj < 0) {
+    g_create_error = "non-positive workspace sizes";
+    return SS_ERR_ARG;
+  }
+  if (cfg->precision != SS_FP64) {
+    g_create_error = "precision mode not available in this build";
+    return SS_ERR_ARG;
+  }
+  if (!(cfg->eta >= 0.0) || !(cfg->decim_tol >= 0.0) || cfg->decim_max_iter < 1) {
+    g_create_error = "invalid eta / decim_tol / decim_max_iter";
+    return SS_ERR_ARG;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) {
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return SS_ERR_CUDA;
+  }
+  std::unique_ptr<ss_handle> h(new ss_handle());
+  h->cfg = *cfg;
+  cudaGetDevice(&h->device);
+  if (cfg->stream) {
+    h->stream = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreate(&h->stream);
+    if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return SS_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  h->arena_bytes = (size_t)cfg->max_points * point_bytes(cfg->n_b_max, cfg->s_b_max, cfg->max_inj);
+  e = cudaMalloc(&h->arena, h->arena_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    g_create_error = "workspace of " + std::to_string(h->arena_bytes) + " bytes: " + cudaGetErrorString(e);
+    return SS_ERR_OOM;
+  }
+  *hp = h.release();
+  return SS_OK;
+}
+
+int ss_set_hamiltonian(ss_handle* h, int k_id, int n_b, int s_b, const ss_c64* H_diag, const ss_c64* H_upper,
+                       const ss_c64* S_diag, const ss_c64* S_upper, const ss_c64* lead_L, const ss_c64* lead_R) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (k_id < 0 || k_id >= MAX_K_ID) return fail(h, SS_ERR_ARG, "k_id outside 0..4095");
+  if (n_b < 1 || s_b < 1 || n_b > h->cfg.n_b_max || s_b > h->cfg.s_b_max)
+    return fail(h, SS_ERR_ARG, "n_b / s_b outside 1..(n_b_max, s_b_max)");
+  if (!H_diag || !S_diag || (n_b > 1 && (!H_upper || !S_upper)))
+    return fail(h, SS_ERR_ARG, "NULL Hamiltonian block array");
+  if (n_b < 2 && (!lead_L || !lead_R)) return fail(h, SS_ERR_ARG, "periodic leads need n_b >= 2");
+  auto it = h->ks.find(k_id);
+  if (it != h->ks.end()) { it->second.free_all(); h->ks.erase(it); }
+  h->c_sigma = h->c_T = false;
+  h->cE.clear();
+  KData kd;
+  kd.n = n_b; kd.s = s_b;
+  const size_t ss2 = (size_t)s_b * s_b;
+  const cudaMemcpyKind kind = h->cfg.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t st = h->stream;
+  auto alloc_copy = [&](z64** dst, const ss_c64* src, size_t cnt) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(cnt, 1) * sizeof(z64));
+    if (e != cudaSuccess || cnt == 0) return e;
+    return cudaMemcpyAsync(*dst, src, cnt * sizeof(z64), kind, st);
+  };
+  cudaError_t e = alloc_copy(&kd.Hd, H_diag, n_b * ss2);
+  if (e == cudaSuccess) e = alloc_copy(&kd.Sd, S_diag, n_b * ss2);
+  if (e == cudaSuccess) e = alloc_copy(&kd.Hu, H_upper, (n_b - 1) * ss2);
+  if (e == cudaSuccess) e = alloc_copy(&kd.Su, S_upper, (n_b - 1) * ss2);
+  if (e == cudaSuccess && (lead_L || lead_R)) e = cudaMalloc(&kd.lead, 8 * ss2 * sizeof(z64));
+  if (e == cudaSuccess && lead_L) e = cudaMemcpyAsync(kd.lead, lead_L, 4 * ss2 * sizeof(z64), kind, st);
+  if (e == cudaSuccess && lead_R) e = cudaMemcpyAsync(kd.lead + 4 * ss2, lead_R, 4 * ss2 * sizeof(z64), kind, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    kd.free_all();
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return fail(h, SS_ERR_OOM, "Hamiltonian storage"); }
+    return cuda_fail(h, e, "ss_set_hamiltonian");
+  }
+  for (int q = 0; q < 2; ++q) {
+    const ss_c64* given = q == 0 ? lead_L : lead_R;
+    if (given) {
+      z64* base = kd.lead + (size_t)q * 4 * ss2;
+      for (int j = 0; j < 4; ++j) kd.cell[q][j] = base + j * ss2;
+    } else {
+      const int cellb = q == 0 ? 0 : n_b - 1;       // end cell
+      const int upb = q == 0 ? 0 : n_b - 2;         // its coupling block
+      kd.cell[q][0] = kd.Hd + cellb * ss2;
+      kd.cell[q][1] = kd.Hu + upb * ss2;
+      kd.cell[q][2] = kd.Sd + cellb * ss2;
+      kd.cell[q][3] = kd.Su + upb * ss2;
+    }
+  }
+  h->ks[k_id] = kd;
+  return SS_OK;
+}
+
+int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id, ss_c64* sigma_L, ss_c64* sigma_R,
+                   int* iters, int* status) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  Want w;
+  w.sigma_out = true;
+  w.sigL = sigma_L;
+  w.sigR = sigma_R;
+  std::vector<int> st, it;
+  std::vector<double> T, Ti;
+  int rc = run_points(h, n_pts, E, k_id, w, st, it, T, Ti);
+  if (rc == SS_ERR_ARG || rc == SS_ERR_STATE || rc == SS_ERR_CUDA || rc == SS_ERR_OOM) {
+    if (st.empty()) return rc;
+  }
+  if (iters) for (size_t i = 0; i < it.size(); ++i) iters[i] = it[i];
+  if (status) for (size_t i = 0; i < st.size(); ++i) status[i] = st[i];
+  if (rc == SS_OK) h->c_T = false;
+  return rc;
+}
+
+int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id, int n_inj, const ss_c64* inj, ss_c64* x,
+             int* status) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (n_inj < 1 || n_inj > h->cfg.max_inj) return fail(h, SS_ERR_ARG, "n_inj outside 1..max_inj");
+  if (!inj) return fail(h, SS_ERR_ARG, "NULL injection");
+  Want w;
+  w.solve = true;
+  w.ninj = n_inj;
+  w.inj = inj;
+  w.x = x;
+  std::vector<int> st, it;
+  std::vector<double> T, Ti;
+  int rc = run_points(h, n_pts, E, k_id, w, st, it, T, Ti);
+  if (status) for (size_t i = 0; i < st.size(); ++i) status[i] = st[i];
+  return rc;
+}
+
+int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, double* T, double* err_est,
+                    int* status) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (!T && n_pts > 0) return fail(h, SS_ERR_ARG, "NULL T");
+  std::vector<double> Tv, Ti;
+  std::vector<int> st, it;
+  int rc = SS_OK;
+  if (h->c_T && same_points(h, n_pts, E, k_id)) {
+    Tv = h->cT;
+    Ti = h->cTi;
+    st = h->c_status;
+    for (int v : st) rc = worst(rc, v);
+  } else {
+    Want w;
+    w.solve = true;
+    rc = run_points(h, n_pts, E, k_id, w, st, it, Tv, Ti);
+    if (st.empty()) return rc;
+  }
+  std::vector<double> err(n_pts);
+  for (int i = 0; i < n_pts; ++i) err[i] = std::fabs(Ti[i]) / std::max(1.0, std::fabs(Tv[i]));
+  if (h->cfg.device_ptrs) {
+    cudaError_t e = cudaMemcpyAsync(T, Tv.data(), sizeof(double) * n_pts, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && err_est)
+      e = cudaMemcpyAsync(err_est, err.data(), sizeof(double) * n_pts, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy T");
+  } else {
+    std::memcpy(T, Tv.data(), sizeof(double) * n_pts);
+    if (err_est) std::memcpy(err_est, err.data(), sizeof(double) * n_pts);
+  }
+  if (status) for (int i = 0; i < n_pts; ++i) status[i] = st[i];
+  return rc;
+}
+
+int ss_destroy(ss_handle* h) {
+  if (!h) return SS_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->ks) kv.second.free_all();
+  h->ks.clear();
+  cudaFree(h->arena);
+  cudaFree(h->dint);
+  cudaFree(h->ddbl);
+  cudaFree(h->dtr);
+  h->p_setup.clear(); h->p_iter[0].clear(); h->p_iter[1].clear();
+  h->p_final.clear(); h->p_sweep.clear(); h->p_bound.clear();
+  h->prof.reset();
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return SS_OK;
+}
+
+const char* ss_last_error(const ss_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
+
+int ss_profile_read(ss_handle* h, int kind, double* total_ms, double* flops, long long* launches) {
+  if (!h) return SS_ERR_ARG;
+  if (kind < 0 || kind > K_MEMSET) return fail(h, SS_ERR_ARG, "unknown kernel kind");
+  h->prof.collect();
+  if (total_ms) *total_ms = h->prof.ms[kind];
+  if (flops) *flops = h->prof.flops[kind];
+  if (launches) *launches = h->prof.launches[kind];
+  return SS_OK;
+}
+
+int ss_profile_reset(ss_handle* h) {
+  if (!h) return SS_ERR_ARG;
+  h->prof.reset();
+  return SS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Batched complex128 GEMM on the FP64 pipe (sm_103a).
+//
+// Used for every product of the FP64 path: the Schur-complement update
+// A_ii - A_{i,i+1} X_{i+1} and the chain Q_i = -X_i Q_{i-1} of Algorithm 1
+// (Sec. 3B), the trailing updates of the blocked LU, the doubling products of
+// the lead self-energies, the 2s x 2s boundary system R = 1 - C Q of Eq. x
+// and the transmission products.
+//
+// Design: one launch covers a group of independent problems of any shapes.
+// CTA b finds its problem by binary search in a prefix table of tile counts.
+// Each CTA owns a 64 x 64 complex output tile, stages 64 x 8 slices of op(A)
+// and op(B) in shared memory and keeps a 4 x 4 complex micro-tile per thread
+// in registers.  On GB300 the FP64 pipe (about 2 DFMA per clock per SM) is the
+// bound by a wide margin, so the kernel spends its effort on keeping every
+// issued instruction a DFMA rather than on deep staging.
+//
+// Operands may be "formed": element = e*S - H read from two matrices, which
+// fuses the assembly of A = E S - H into the loads (no A is ever stored).
+#include "ss_internal.cuh"
+
+namespace ss {
+
+namespace {
+constexpr int TM = 64, TN = 64, TK = 8, NT = 256;
+
+__device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, int nprob, int bid) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(tile_start + mid) <= bid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// element (i, j) of op(X)
+__device__ __forceinline__ z64 op_load(const Operand& o, int i, int j) {
+  size_t idx = o.trans ? (size_t)j * o.ld + i : (size_t)i * o.ld + j;
+  z64 v = o.p[idx];
+  if (o.s) v = zsub(zmul(o.e, o.s[idx]), v);
+  return o.trans ? zconj(v) : v;
+}
+
+__global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ descs,
+                                                   const int* __restrict__ tile_start, int nprob) {
+  __shared__ z64 As[TK][TM];
+  __shared__ z64 Bs[TK][TN];
+  const int pid = find_problem(tile_start, nprob, blockIdx.x);
+  const GemmDesc& d = descs[pid];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int m = d.m, n = d.n, K = d.k;
+  const int tiles_n = (n + TN - 1) / TN;
+  const int t = blockIdx.x - __ldg(tile_start + pid);
+  const int row0 = (t / tiles_n) * TM, col0 = (t % tiles_n) * TN;
+  const Operand a = d.a, b = d.b;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+  z64 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = zmk(0.0, 0.0);
+
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = tid; e < TM * TK; e += NT) {
+      int r, kk;
+      if (a.trans) { kk = e / TM; r = e % TM; } else { r = e / TK; kk = e % TK; }
+      const int gi = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gi < m && gk < K) ? op_load(a, gi, gk) : zmk(0.0, 0.0);
+    }
+    for (int e = tid; e < TK * TN; e += NT) {
+      int c, kk;
+      if (b.trans) { c = e / TK; kk = e % TK; } else { kk = e / TN; c = e % TN; }
+      const int gj = col0 + c, gk = k0 + kk;
+      Bs[kk][c] = (gj < n && gk < K) ? op_load(b, gk, gj) : zmk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      z64 av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zfma(acc[i][j], av[i], bv[j]);
+    }
+    __syncthreads();
+  }
+
+  const z64 alpha = d.alpha, beta = d.beta;
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= n) continue;
+      z64 v = zmul(alpha, acc[i][j]);
+      if (d.cmode == 1) {
+        const size_t fi = (size_t)r * d.ldcf + c;
+        v = zadd(v, zmul(beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
+      } else if (d.cmode == 2) {
+        if (r == c) v = zadd(v, beta);
+      } else if (use_beta) {
+        v = zadd(v, zmul(beta, d.c[(size_t)r * d.ldc + c]));
+      }
+      d.c[(size_t)r * d.ldc + c] = v;
+    }
+  }
+}
+}  // namespace
+
+int zgemm_tiles(int m, int n) {
+  if (m <= 0 || n <= 0) return 0;
+  return ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
+}
+
+void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
+                  cudaStream_t st) {
+  if (nprob <= 0 || total_tiles <= 0) return;
+  zgemm_kernel<<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+}
+
+}  // namespace ss

@@ -1,0 +1,234 @@
+// Batched blocked LU with partial pivoting and fused right-hand-side solve.
+//
+// Each problem is a row-major s x ncols matrix W = [D | B]; the kernels
+// factor P D = L U in place and overwrite B with D^-1 B.  This is the
+// "one LU factorization and one backward substitution" per block of
+// Algorithm 1 (Sec. 3B, Sec. 3C), with row pivoting added: the paper's
+// zgesv_nopiv has none.  Pivot: largest |re| + |im| in the column, lowest row
+// on ties (any stable order gives the same x).
+//
+// Per panel of nb <= 32 columns starting at k0 (right-looking):
+//   lu_panel    one CTA per problem factors rows k0..s-1 of the panel;
+//   lu_rowblock applies the panel's row swaps to every other column and
+//               forms U12 = L11^-1 A12 (and L11^-1 B1) in place;
+//   (zgemm)     A22 -= L21 U12 over the trailing columns, RHS included.
+// After the last panel, B holds L^-1 P B; per panel from the bottom:
+//   lu_backsub_diag  B_k = U_kk^-1 B_k,  (zgemm) B_0..k -= U_0..k,k B_k.
+//
+// A zero or non-finite pivot records 1 + its column in *info (first one
+// only) and the elimination continues with a zero reciprocal, so no problem
+// can stall the group.
+#include "ss_internal.cuh"
+
+namespace ss {
+
+namespace {
+constexpr int PANEL_THREADS = 512;
+constexpr int NWARP = PANEL_THREADS / 32;
+constexpr int MAXNB = 32;
+
+__global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(const LuDesc* __restrict__ descs,
+                                                                 int k0, int nb) {
+  const LuDesc d = descs[blockIdx.x];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(nb, s - k0);
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  __shared__ double red_v[NWARP];
+  __shared__ int red_i[NWARP];
+  __shared__ int red_bad[NWARP];
+  __shared__ z64 prow[MAXNB];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int j = 0; j < nbw; ++j) {
+    const int col = k0 + j;
+    // --- pivot search over rows col..s-1
+    double best = -1.0;
+    int bi = s;
+    int bad_elem = 0;
+    for (int r = col + tid; r < s; r += PANEL_THREADS) {
+      const z64 v = w[(size_t)r * ld + col];
+      const double a = fabs(v.x) + fabs(v.y);
+      if (!(a <= 1.7976931348623157e308)) bad_elem = 1;  // NaN or Inf in the column
+      if (a > best) { best = a; bi = r; }
+    }
+    bad_elem = __any_sync(0xffffffffu, bad_elem);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; red_bad[warp] = bad_elem; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = red_v[0];
+      int bix = red_i[0];
+      int anybad = red_bad[0];
+      for (int q = 1; q < NWARP; ++q) {
+        if (red_v[q] > bv || (red_v[q] == bv && red_i[q] < bix)) { bv = red_v[q]; bix = red_i[q]; }
+        anybad |= red_bad[q];
+      }
+      const bool bad = anybad || !(bv > 0.0) || !isfinite(bv) || bix >= s;
+      if (bix >= s) bix = col;
+      if (bad && d.info && *d.info == 0) *d.info = col + 1;
+      d.ipiv[col] = bix;
+      s_piv = bix;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != col && tid < nbw) {
+      z64* a = w + (size_t)col * ld + k0 + tid;
+      z64* b = w + (size_t)p * ld + k0 + tid;
+      const z64 t = *a;
+      *a = *b;
+      *b = t;
+    }
+    __syncthreads();
+    if (tid < nbw) prow[tid] = w[(size_t)col * ld + k0 + tid];
+    __syncthreads();
+    const z64 inv = zinv(prow[j]);
+    const z64 pr = (lane < nbw) ? prow[lane] : zmk(0.0, 0.0);
+    // --- scale the column and update the rest of the panel, one row per warp
+    for (int r = col + 1 + warp; r < s; r += NWARP) {
+      z64* rowp = w + (size_t)r * ld + k0;
+      const z64 l = zmul(rowp[j], inv);
+      if (lane == j) rowp[j] = l;
+      else if (lane > j && lane < nbw) rowp[lane] = zsub(rowp[lane], zmul(l, pr));
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int RB_THREADS = 128;
+
+// Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
+// columns to its right (right-hand sides included).
+__global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* __restrict__ descs,
+                                                                 int k0, int nb) {
+  const LuDesc d = descs[blockIdx.y];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(nb, s - k0);
+  __shared__ z64 Ls[MAXNB][MAXNB + 1];
+  __shared__ int piv[MAXNB];
+  for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
+    const int r = e / nbw, c = e % nbw;
+    Ls[r][c] = d.w[(size_t)(k0 + r) * d.ldw + k0 + c];
+  }
+  if (threadIdx.x < nbw) piv[threadIdx.x] = d.ipiv[k0 + threadIdx.x];
+  __syncthreads();
+  const int q = blockIdx.x * RB_THREADS + threadIdx.x;
+  const int nout = d.ncols - nbw;
+  if (q >= nout) return;
+  const int c = (q < k0) ? q : q + nbw;
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  for (int j = 0; j < nbw; ++j) {
+    const int p = piv[j];
+    if (p != k0 + j) {
+      z64* a = w + (size_t)(k0 + j) * ld + c;
+      z64* b = w + (size_t)p * ld + c;
+      const z64 t = *a;
+      *a = *b;
+      *b = t;
+    }
+  }
+  if (c < k0) return;
+  z64 x[MAXNB];
+#pragma unroll
+  for (int j = 0; j < MAXNB; ++j)
+    if (j < nbw) x[j] = w[(size_t)(k0 + j) * ld + c];
+#pragma unroll
+  for (int j = 1; j < MAXNB; ++j) {
+    if (j < nbw) {
+      z64 acc = x[j];
+#pragma unroll
+      for (int i = 0; i < MAXNB; ++i)
+        if (i < j) {
+          const z64 l = Ls[j][i];
+          acc.x = fma(-l.x, x[i].x, acc.x);
+          acc.x = fma(l.y, x[i].y, acc.x);
+          acc.y = fma(-l.x, x[i].y, acc.y);
+          acc.y = fma(-l.y, x[i].x, acc.y);
+        }
+      x[j] = acc;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MAXNB; ++j)
+    if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
+}
+
+// B_k = U_kk^-1 B_k on the right-hand-side columns (backward substitution
+// within one diagonal block of U).
+__global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDesc* __restrict__ descs,
+                                                                     int k0, int nb) {
+  const LuDesc d = descs[blockIdx.y];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(nb, s - k0);
+  __shared__ z64 Us[MAXNB][MAXNB + 1];
+  __shared__ z64 dinv[MAXNB];
+  for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
+    const int r = e / nbw, c = e % nbw;
+    Us[r][c] = d.w[(size_t)(k0 + r) * d.ldw + k0 + c];
+  }
+  __syncthreads();
+  if (threadIdx.x < nbw) dinv[threadIdx.x] = zinv(Us[threadIdx.x][threadIdx.x]);
+  __syncthreads();
+  const int q = blockIdx.x * RB_THREADS + threadIdx.x;
+  const int nrhs = d.ncols - s;
+  if (q >= nrhs) return;
+  const int c = s + q;
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  z64 x[MAXNB];
+#pragma unroll
+  for (int j = 0; j < MAXNB; ++j)
+    if (j < nbw) x[j] = w[(size_t)(k0 + j) * ld + c];
+#pragma unroll
+  for (int j = MAXNB - 1; j >= 0; --j) {
+    if (j < nbw) {
+      z64 acc = x[j];
+#pragma unroll
+      for (int i = 0; i < MAXNB; ++i)
+        if (i > j && i < nbw) {
+          const z64 u = Us[j][i];
+          acc.x = fma(-u.x, x[i].x, acc.x);
+          acc.x = fma(u.y, x[i].y, acc.x);
+          acc.y = fma(-u.x, x[i].y, acc.y);
+          acc.y = fma(-u.y, x[i].x, acc.y);
+        }
+      x[j] = zmul(acc, dinv[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MAXNB; ++j)
+    if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
+}
+}  // namespace
+
+void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, cudaStream_t st) {
+  if (nprob <= 0) return;
+  lu_panel_kernel<<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
+}
+
+void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int max_cols, cudaStream_t st) {
+  if (nprob <= 0 || max_cols <= 0) return;
+  dim3 grid((max_cols + RB_THREADS - 1) / RB_THREADS, nprob);
+  lu_rowblock_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+}
+
+void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs, cudaStream_t st) {
+  if (nprob <= 0 || max_rhs <= 0) return;
+  dim3 grid((max_rhs + RB_THREADS - 1) / RB_THREADS, nprob);
+  lu_backsub_diag_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+}
+
+}  // namespace ss

@@ -1,0 +1,162 @@
+// Launch plans: a recorded list of grouped kernel launches whose descriptors
+// live in one device buffer.  A plan is built on the host, uploaded with a
+// single copy and then run eagerly or captured once into a CUDA graph and
+// replayed (the doubling iterations of the self-energy step).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+// Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
+enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
+                  K_FILL, K_MEMSET };
+
+struct LaunchRec {
+  LaunchKind kind;
+  size_t off = 0, toff = 0;  // descriptor / tile-table offsets in the plan buffer
+  int nprob = 0, tiles = 0;
+  int k0 = 0, nb = 0, maxc = 0;
+  double tol = 0.0;
+  int cap = 0, count = 0, ival = 0;
+  void* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t bytes = 0;
+};
+
+// Optional per-launch timing: a CUDA event pair around every launch, with
+// the algorithmic flops of GEMM launches counted only for problems whose
+// `active` flag (mirrored on the host) is set.
+struct Prof {
+  struct Rec { int kind; cudaEvent_t a, b; double flops; };
+  std::vector<Rec> recs;
+  const int* act_dev = nullptr;   // device flag array the descriptors point into
+  const int* act_host = nullptr;  // host mirror of it at launch time
+  int nact = 0;
+  double ms[K_MEMSET + 1] = {0};
+  double flops[K_MEMSET + 1] = {0};
+  long long launches[K_MEMSET + 1] = {0};
+  // Fold finished records into the totals (call after a stream sync).
+  void collect() {
+    for (auto& r : recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.kind] += t;
+      flops[r.kind] += r.flops;
+      launches[r.kind] += 1;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  void reset() {
+    collect();
+    for (int i = 0; i <= K_MEMSET; ++i) { ms[i] = 0; flops[i] = 0; launches[i] = 0; }
+  }
+};
+
+class Plan {
+ public:
+  ~Plan() { release(); }
+  void clear() {
+    host_.clear();
+    recs_.clear();
+    destroy_graph();
+  }
+  size_t push(const void* data, size_t bytes) {
+    size_t off = (host_.size() + 15) & ~size_t(15);
+    host_.resize(off + bytes);
+    if (bytes) std::memcpy(host_.data() + off, data, bytes);
+    return off;
+  }
+  template <class D>
+  size_t push_vec(const std::vector<D>& v) { return push(v.data(), v.size() * sizeof(D)); }
+
+  void gemm(const std::vector<GemmDesc>& ds) {
+    if (ds.empty()) return;
+    std::vector<int> start(ds.size());
+    int tot = 0;
+    for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zgemm_tiles(ds[i].m, ds[i].n); }
+    if (tot == 0) return;
+    LaunchRec r;
+    r.kind = K_GEMM;
+    r.off = push_vec(ds);
+    r.toff = push_vec(start);
+    r.nprob = (int)ds.size();
+    r.tiles = tot;
+    recs_.push_back(r);
+  }
+  void form(const std::vector<FormDesc>& ds) {
+    if (ds.empty()) return;
+    std::vector<int> start(ds.size());
+    int tot = 0;
+    for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zform_tiles(ds[i].rows, ds[i].cols); }
+    if (tot == 0) return;
+    LaunchRec r;
+    r.kind = K_FORM;
+    r.off = push_vec(ds);
+    r.toff = push_vec(start);
+    r.nprob = (int)ds.size();
+    r.tiles = tot;
+    recs_.push_back(r);
+  }
+  // Blocked LU + solve of every problem in ds (panel width nb <= 32).
+  void lu_solve(const std::vector<LuDesc>& ds, int nb);
+  void norm1(const std::vector<Norm1Desc>& ds) {
+    if (ds.empty()) return;
+    LaunchRec r;
+    r.kind = K_NORM1;
+    r.off = push_vec(ds);
+    r.nprob = (int)ds.size();
+    for (auto& d : ds) r.maxc = d.cols > r.maxc ? d.cols : r.maxc;
+    recs_.push_back(r);
+  }
+  void trace(const std::vector<TraceDesc>& ds) {
+    if (ds.empty()) return;
+    LaunchRec r;
+    r.kind = K_TRACE;
+    r.off = push_vec(ds);
+    r.nprob = (int)ds.size();
+    recs_.push_back(r);
+  }
+  void check(double* na, double* nb, const double* nd, int* act, int* iters, int* conv, int nprob,
+             double tol, int cap, int count) {
+    LaunchRec r;
+    r.kind = K_CHECK;
+    r.p[0] = na; r.p[1] = nb; r.p[2] = (void*)nd; r.p[3] = act; r.p[4] = iters; r.p[5] = conv;
+    r.nprob = nprob; r.tol = tol; r.cap = cap; r.count = count;
+    recs_.push_back(r);
+  }
+  void fill(int* p, int n, int v) {
+    LaunchRec r;
+    r.kind = K_FILL;
+    r.p[0] = p; r.nprob = n; r.ival = v;
+    recs_.push_back(r);
+  }
+  void memset0(void* p, size_t bytes) {
+    LaunchRec r;
+    r.kind = K_MEMSET;
+    r.p[0] = p; r.bytes = bytes;
+    recs_.push_back(r);
+  }
+
+  cudaError_t upload(cudaStream_t st);
+  cudaError_t run(cudaStream_t st, long long* nlaunch, Prof* prof = nullptr);
+  // Capture run() into a graph on first use, then replay it.
+  cudaError_t replay(cudaStream_t st, long long* nlaunch);
+  bool empty() const { return recs_.empty(); }
+
+ private:
+  void release();
+  void destroy_graph();
+  std::vector<unsigned char> host_;
+  std::vector<LaunchRec> recs_;
+  unsigned char* dev_ = nullptr;
+  size_t devcap_ = 0;
+  cudaGraphExec_t exec_ = nullptr;
+  long long graph_kernels_ = 0;
+};
+
+}  // namespace ss
