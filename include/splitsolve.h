@@ -144,6 +144,18 @@ const char* ss_last_error(const ss_handle* h);
  * ss_create (graph replays count their kernel nodes). */
 long long ss_launch_count(const ss_handle* h);
 
+/* Transmission from caller-provided blocks (the Caroli trace of the
+ * transmission step): T[p] = Re Tr[Gamma_L G_1n Gamma_R G_1n^H] with
+ * Gamma = i (Sigma - Sigma^H), for n_pts points of block size s_b.
+ * sigma_L, sigma_R, G1n: DEVICE pointers, s_b*s_b complex per point, packed;
+ * T: DEVICE pointer, n_pts doubles.  Scratch (4*s_b^2 + 1 complex per point)
+ * is allocated with cudaMallocAsync on `stream` (a cudaStream_t, NULL = legacy
+ * stream) and released before return; the call synchronises `stream`.
+ * Errors: SS_ERR_ARG (sizes, NULL), SS_ERR_OOM, SS_ERR_CUDA; the message is
+ * in ss_last_error(NULL). */
+int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R,
+                           const ss_c64* G1n, double* T, void* stream);
+
 /* Kernel kinds for ss_profile_read. */
 #define SS_KERNEL_ZGEMM      0  /* batched complex GEMM (all GEMM-shaped steps)      */
 #define SS_KERNEL_FORM       1  /* elementwise forms / copies                         */

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGU
 
 EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
            "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
-           "ss_profile_reset")
+           "ss_profile_reset", "ss_caroli_transmission")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6}
 
 
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH):
     lib.ss_profile_read.restype = C.c_int
     lib.ss_profile_reset.argtypes = [vp]
     lib.ss_profile_reset.restype = C.c_int
+    lib.ss_caroli_transmission.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
+    lib.ss_caroli_transmission.restype = C.c_int
     for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
                  "ss_destroy"):
         getattr(lib, name).restype = C.c_int
@@ -259,3 +261,12 @@ class Handle:
 
 def ss_create(**kw) -> Handle:
     return Handle(**kw)
+
+
+def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):
+    """T[p] = Re Tr[Gamma_L G Gamma_R G^H]; torch CUDA tensors (P,s,s) complex128 and (P,) float64."""
+    lib = load_library()
+    P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
+    rc = lib.ss_caroli_transmission(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
+    if rc != SS_OK:
+        raise SSError(rc, lib.ss_last_error(None).decode())

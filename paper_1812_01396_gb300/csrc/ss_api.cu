@@ -750,6 +750,32 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
 
 }  // namespace
 
+namespace ss {
+size_t caroli_scratch_elems(int n_pts, int s) { return (size_t)n_pts * (4 * (size_t)s * s + 1); }
+
+void caroli_descriptors(int n_pts, int s, const z64* sigL, const z64* sigR, const z64* G, z64* scratch,
+                        std::vector<FormDesc>& f, std::vector<GemmDesc>& g, std::vector<TraceDesc>& t) {
+  const size_t ss2 = (size_t)s * s;
+  z64* traces = scratch + (size_t)n_pts * 4 * ss2;
+  for (int p = 0; p < n_pts; ++p) {
+    z64* base = scratch + (size_t)p * 4 * ss2;
+    z64 *gl = base, *gr = base + ss2, *m1 = base + 2 * ss2, *m2 = base + 3 * ss2;
+    const z64* sig[2] = {sigL + p * ss2, sigR + p * ss2};
+    z64* gam[2] = {gl, gr};
+    for (int q = 0; q < 2; ++q) {
+      FormDesc gm = fdesc(gam[q], s, s, s);
+      gm.x = sig[q]; gm.ldx = s; gm.ax = make_double2(0.0, 1.0);
+      gm.y = sig[q]; gm.ldy = s; gm.ty = 1; gm.ay = make_double2(0.0, -1.0);
+      f.push_back(gm);
+    }
+    const z64* Gp = G + p * ss2;
+    g.push_back(gdesc(s, s, s, plain(gl, s), plain(Gp, s), m1, s, ONE, ZERO));
+    g.push_back(gdesc(s, s, s, plain(gr, s), plain(Gp, s, 1), m2, s, ONE, ZERO));
+    t.push_back({m1, s, m2, s, s, traces + p, nullptr});
+  }
+}
+}  // namespace ss
+
 // ======================================================================= C ABI
 extern "C" {
 
@@ -968,6 +994,36 @@ const char* ss_last_error(const ss_handle* h) {
 }
 
 long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
+
+int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R, const ss_c64* G1n,
+                           double* T, void* stream) {
+  if (n_pts < 0 || s_b < 1) { g_create_error = "ss_caroli_transmission: bad sizes"; return SS_ERR_ARG; }
+  if (n_pts == 0) return SS_OK;
+  if (!sigma_L || !sigma_R || !G1n || !T) { g_create_error = "ss_caroli_transmission: NULL array"; return SS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  z64* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, caroli_scratch_elems(n_pts, s_b) * sizeof(z64), st);
+  if (e != cudaSuccess) { cudaGetLastError(); g_create_error = "ss_caroli_transmission: scratch"; return SS_ERR_OOM; }
+  std::vector<FormDesc> f;
+  std::vector<GemmDesc> g;
+  std::vector<TraceDesc> t;
+  caroli_descriptors(n_pts, s_b, reinterpret_cast<const z64*>(sigma_L), reinterpret_cast<const z64*>(sigma_R),
+                     reinterpret_cast<const z64*>(G1n), scratch, f, g, t);
+  Plan plan;
+  plan.form(f);
+  plan.gemm(g);
+  plan.trace(t);
+  e = plan.upload(st);
+  if (e == cudaSuccess) e = plan.run(st, nullptr);
+  if (e == cudaSuccess) {
+    launch_real_part(scratch + (size_t)n_pts * 4 * s_b * s_b, T, n_pts, st);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { g_create_error = std::string("ss_caroli_transmission: ") + cudaGetErrorString(e); return SS_ERR_CUDA; }
+  return SS_OK;
+}
 
 int ss_profile_read(ss_handle* h, int kind, double* total_ms, double* flops, long long* launches) {
   if (!h) return SS_ERR_ARG;

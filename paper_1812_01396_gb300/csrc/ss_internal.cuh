@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace ss {
 
 typedef double2 z64;
@@ -129,5 +131,13 @@ void launch_decim_check(double* na, double* nb, const double* nd, int* act, int*
                         int* conv, int nprob, double tol, int cap, int count, cudaStream_t st);
 
 void launch_fill_i32(int* p, int n, int v, cudaStream_t st);
+void launch_real_part(const z64* in, double* out, int n, cudaStream_t st);
+
+// Descriptors of the Caroli trace T = Re Tr[Gamma_L G Gamma_R G^H] for n_pts
+// points of size s, with scratch laid out as [GamL | GamR | M1 | M2] per point
+// (4 s^2 complex) followed by n_pts complex traces.  Fills the host vectors.
+void caroli_descriptors(int n_pts, int s, const z64* sigL, const z64* sigR, const z64* G, z64* scratch,
+                        std::vector<FormDesc>& f, std::vector<GemmDesc>& g, std::vector<TraceDesc>& t);
+size_t caroli_scratch_elems(int n_pts, int s);
 
 }  // namespace ss

@@ -123,11 +123,21 @@ __global__ void decim_check_kernel(double* __restrict__ na, double* __restrict__
   conv[p] = c ? 1 : 0;
   if (c || iters[p] >= cap || m != m || a != a || b != b) act[p] = 0;
 }
+__global__ void real_part_kernel(const z64* __restrict__ in, double* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i].x;
+}
+
 __global__ void fill_i32_kernel(int* p, int n, int v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
 }
 }  // namespace
+
+void launch_real_part(const z64* in, double* out, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  real_part_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+}
 
 void launch_fill_i32(int* p, int n, int v, cudaStream_t st) {
   if (n <= 0) return;

@@ -284,3 +284,15 @@ def test_workspace_too_large_is_oom(ss):
     with pytest.raises(ss.SSError) as e:
         ss.Handle(n_b_max=100000, s_b_max=4096, max_points=64)
     assert e.value.code == ss.SS_ERR_OOM
+
+
+def test_caroli_transmission_entry_point(ss):
+    """T from caller-provided Sigma_L, Sigma_R, G_1n (oracle values) on the device."""
+    import torch
+    pts = [(synth.make_device(4, 40, seed=20)[0], 0.3), (synth.make_device(4, 40, seed=21)[0], -0.5)]
+    refs = [dense.solve_point(d, E) for d, E in pts]
+    t = lambda key: torch.from_numpy(np.stack([r[key] for r in refs])).cuda()
+    T = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ss.ss_caroli_transmission(t("sigma_L"), t("sigma_R"), t("G1n"), T)
+    for p, r in enumerate(refs):
+        assert dense.rel_T_err(float(T[p].item()), r["T"]) < 1e-12
