@@ -31,7 +31,7 @@ using namespace ss;
 
 namespace {
 
-constexpr int LU_NB = 32;
+constexpr int LU_NB = 0;  // panel width chosen per group from its largest block
 constexpr int MAX_K_ID = 4096;
 
 std::string g_create_error;

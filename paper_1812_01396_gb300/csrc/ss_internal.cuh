@@ -116,7 +116,10 @@ void launch_zform(const FormDesc* d, const int* tile_start, int nprob, int total
                   cudaStream_t st);
 int zform_tiles(int rows, int cols);
 
-void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, cudaStream_t st);
+// Panel width used for a group whose largest block is smax (keeps the
+// register-resident panel kernel within 32 complex values per thread).
+int lu_panel_width(int smax);
+void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st);
 void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int max_cols,
                         cudaStream_t st);
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs,

@@ -103,6 +103,145 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(const LuDesc* _
   }
 }
 
+// Register-resident panel: thread t keeps rows k0 + t + 512 q (q < RPT) of
+// the panel, all NB columns, in registers for the whole factorisation; the
+// pivot row and the row it replaces are exchanged through shared memory.
+// Three barriers per column and no global traffic between load and store.
+// Needs s - k0 <= 512 * RPT and NB * RPT <= 16 complex values per thread
+// (64 registers of data).
+// The column loop is a compile-time recursion so every register index is a
+// constant.
+struct PanelShared {
+  double red_v[NWARP];
+  int red_i[NWARP];
+  int red_bad[NWARP];
+  z64 prow[MAXNB];
+  z64 crow[MAXNB];
+  int piv;
+};
+
+template <int NB, int RPT, int J>
+struct PanelStep {
+  static __device__ __forceinline__ void run(z64 (&a)[RPT][NB], const int (&rows)[RPT], PanelShared& sh,
+                                             const LuDesc& d, int k0, int nbw, int s) {
+    if (J < nbw) {
+      const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+      const int col = k0 + J;
+      double best = -1.0;
+      int bi = s, bad = 0;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        if (rows[q] >= col && rows[q] < s) {
+          const double v = fabs(a[q][J].x) + fabs(a[q][J].y);
+          if (!(v <= 1.7976931348623157e308)) bad = 1;
+          if (v > best) { best = v; bi = rows[q]; }
+        }
+      }
+      bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { sh.red_v[warp] = best; sh.red_i[warp] = bi; sh.red_bad[warp] = bad; }
+      __syncthreads();
+      if (tid == 0) {
+        double bv = sh.red_v[0];
+        int bix = sh.red_i[0], anybad = sh.red_bad[0];
+        for (int q = 1; q < NWARP; ++q) {
+          if (sh.red_v[q] > bv || (sh.red_v[q] == bv && sh.red_i[q] < bix)) { bv = sh.red_v[q]; bix = sh.red_i[q]; }
+          anybad |= sh.red_bad[q];
+        }
+        const bool badp = anybad || !(bv > 0.0) || !isfinite(bv) || bix >= s;
+        if (bix >= s) bix = col;
+        if (badp && d.info && *d.info == 0) *d.info = col + 1;
+        d.ipiv[col] = bix;
+        sh.piv = bix;
+      }
+      __syncthreads();
+      const int p = sh.piv;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        if (rows[q] == p) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) sh.prow[c] = a[q][c];
+        }
+        if (rows[q] == col && p != col) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) sh.crow[c] = a[q][c];
+        }
+      }
+      __syncthreads();
+      if (p != col) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          if (rows[q] == col) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[q][c] = sh.prow[c];
+          } else if (rows[q] == p) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[q][c] = sh.crow[c];
+          }
+        }
+      }
+      const z64 inv = zinv(sh.prow[J]);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        if (rows[q] > col && rows[q] < s) {
+          const z64 l = zmul(a[q][J], inv);
+          a[q][J] = l;
+#pragma unroll
+          for (int c = J + 1; c < NB; ++c) {
+            const z64 u = sh.prow[c];
+            a[q][c].x = fma(-l.x, u.x, a[q][c].x);
+            a[q][c].x = fma(l.y, u.y, a[q][c].x);
+            a[q][c].y = fma(-l.x, u.y, a[q][c].y);
+            a[q][c].y = fma(-l.y, u.x, a[q][c].y);
+          }
+        }
+      }
+    }
+    PanelStep<NB, RPT, J + 1>::run(a, rows, sh, d, k0, nbw, s);
+  }
+};
+
+template <int NB, int RPT>
+struct PanelStep<NB, RPT, NB> {
+  static __device__ __forceinline__ void run(z64 (&)[RPT][NB], const int (&)[RPT], PanelShared&, const LuDesc&,
+                                             int, int, int) {}
+};
+
+template <int NB, int RPT>
+__global__ void __launch_bounds__(PANEL_THREADS, 1) lu_panel_reg_kernel(const LuDesc* __restrict__ descs,
+                                                                     int k0, int nb) {
+  const LuDesc d = descs[blockIdx.x];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(min(nb, NB), s - k0);
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  __shared__ PanelShared sh;
+  z64 a[RPT][NB];
+  int rows[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    rows[q] = k0 + threadIdx.x + q * PANEL_THREADS;
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      a[q][c] = (rows[q] < s && c < nbw) ? w[(size_t)rows[q] * ld + k0 + c] : zmk(0.0, 0.0);
+  }
+  PanelStep<NB, RPT, 0>::run(a, rows, sh, d, k0, nbw, s);
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+    if (rows[q] < s) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nbw) w[(size_t)rows[q] * ld + k0 + c] = a[q][c];
+    }
+}
+
 constexpr int RB_THREADS = 128;
 
 // Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
@@ -214,9 +353,18 @@ __global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDes
 }
 }  // namespace
 
-void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, cudaStream_t st) {
+int lu_panel_width(int smax) {
+  if (smax <= 512) return 16;
+  if (smax <= 1024) return 8;
+  return 32;
+}
+
+void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st) {
   if (nprob <= 0) return;
-  lu_panel_kernel<<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
+  const int h = smax - k0;  // rows of the tallest panel in the group
+  if (nb <= 16 && h <= PANEL_THREADS) lu_panel_reg_kernel<16, 1><<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
+  else if (nb <= 8 && h <= 2 * PANEL_THREADS) lu_panel_reg_kernel<8, 2><<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
+  else lu_panel_kernel<<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
 }
 
 void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int max_cols, cudaStream_t st) {

@@ -11,11 +11,12 @@ void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb) {
   const int np = (int)ds.size();
   int smax = 0;
   for (auto& d : ds) smax = std::max(smax, d.s);
+  if (nb <= 0) nb = lu_panel_width(smax);
   // forward: panels left to right
   for (int k0 = 0; k0 < smax; k0 += nb) {
     LaunchRec r;
     r.kind = K_LU_PANEL;
-    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb;
+    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = smax;
     recs_.push_back(r);
     int maxc = 0;
     std::vector<GemmDesc> g;
@@ -129,7 +130,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     switch (r.kind) {
       case K_GEMM: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
-      case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, st); ++n; break;
+      case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_LU_ROW:
         if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; }
         break;

@@ -102,7 +102,8 @@ class Plan {
     r.tiles = tot;
     recs_.push_back(r);
   }
-  // Blocked LU + solve of every problem in ds (panel width nb <= 32).
+  // Blocked LU + solve of every problem in ds (panel width nb <= 32; nb <= 0
+  // picks the width from the largest block of the group).
   void lu_solve(const std::vector<LuDesc>& ds, int nb);
   void norm1(const std::vector<Norm1Desc>& ds) {
     if (ds.empty()) return;
