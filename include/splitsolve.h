@@ -144,6 +144,17 @@ const char* ss_last_error(const ss_handle* h);
  * ss_create (graph replays count their kernel nodes). */
 long long ss_launch_count(const ss_handle* h);
 
+/* Complex GEMM with the library's kernels: C = op(A) op(B), op = identity or
+ * conjugate transpose (transA / transB = 1), all DEVICE pointers, row-major
+ * with leading dimensions lda, ldb, ldc (elements).  precision SS_FP64 runs
+ * the FP64 kernel of the FP64 path; SS_MIXED_BF16X3 / X6 run the split-BF16
+ * tcgen05 kernel of the mixed path (packing scratch allocated with
+ * cudaMallocAsync on `stream`).  The call synchronises `stream`.
+ * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_TIMEOUT (a bounded
+ * pipeline wait inside the tensor-core kernel expired). */
+int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
+             int transB, ss_c64* C, int ldc, void* stream);
+
 /* Transmission from caller-provided blocks (the Caroli trace of the
  * transmission step): T[p] = Re Tr[Gamma_L G_1n Gamma_R G_1n^H] with
  * Gamma = i (Sigma - Sigma^H), for n_pts points of block size s_b.

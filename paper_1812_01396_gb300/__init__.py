@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGU
 
 EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
            "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
-           "ss_profile_reset", "ss_caroli_transmission")
+           "ss_profile_reset", "ss_zgemm", "ss_caroli_transmission")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6}
 
 
@@ -76,6 +76,9 @@ def load_library(path: str = LIB_PATH):
     lib.ss_profile_read.restype = C.c_int
     lib.ss_profile_reset.argtypes = [vp]
     lib.ss_profile_reset.restype = C.c_int
+    lib.ss_zgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp,
+                             C.c_int, vp]
+    lib.ss_zgemm.restype = C.c_int
     lib.ss_caroli_transmission.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.ss_caroli_transmission.restype = C.c_int
     for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
@@ -102,6 +105,17 @@ def _ptr(a):
 
 def _host_c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _dev_in(t):
+    """Device input: the library reads dense row-major blocks, so make it contiguous."""
+    return t if t.is_contiguous() else t.contiguous()
+
+
+def _dev_out(t):
+    if not t.is_contiguous():
+        raise ValueError("output tensors must be contiguous (dense row-major)")
+    return t
 
 
 class Handle:
@@ -166,6 +180,10 @@ class Handle:
             H_up, S_up = _host_c128(H_up), _host_c128(S_up)
             lead_L = None if lead_L is None else _host_c128(lead_L)
             lead_R = None if lead_R is None else _host_c128(lead_R)
+        else:
+            H_diag, S_diag, H_up, S_up = _dev_in(H_diag), _dev_in(S_diag), _dev_in(H_up), _dev_in(S_up)
+            lead_L = None if lead_L is None else _dev_in(lead_L)
+            lead_R = None if lead_R is None else _dev_in(lead_R)
         rc = self._lib.ss_set_hamiltonian(self._h, int(k_id), n_b, s, _ptr(H_diag), _ptr(H_up), _ptr(S_diag),
                                           _ptr(S_up), _ptr(lead_L), _ptr(lead_R))
         self._check(rc)
@@ -263,10 +281,25 @@ def ss_create(**kw) -> Handle:
     return Handle(**kw)
 
 
+def ss_zgemm(A, B, C, precision=SS_FP64, transA=False, transB=False, stream=None):
+    """C = op(A) op(B) with the library kernels (torch CUDA complex128 tensors, row-major)."""
+    lib = load_library()
+    A, B, C = _dev_in(A), _dev_in(B), _dev_out(C)
+    m = int(A.shape[1] if transA else A.shape[0])
+    k = int(A.shape[0] if transA else A.shape[1])
+    n = int(B.shape[0] if transB else B.shape[1])
+    rc = lib.ss_zgemm(int(precision), m, n, k, _ptr(A), int(A.stride(0)), int(transA), _ptr(B), int(B.stride(0)),
+                      int(transB), _ptr(C), int(C.stride(0)), stream)
+    if rc != SS_OK:
+        raise SSError(rc, lib.ss_last_error(None).decode())
+
+
 def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):
     """T[p] = Re Tr[Gamma_L G Gamma_R G^H]; torch CUDA tensors (P,s,s) complex128 and (P,) float64."""
     lib = load_library()
+    sigma_L, sigma_R, G1n, T = _dev_in(sigma_L), _dev_in(sigma_R), _dev_in(G1n), _dev_out(T)
     P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
     rc = lib.ss_caroli_transmission(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
     if rc != SS_OK:
         raise SSError(rc, lib.ss_last_error(None).decode())
+

@@ -26,6 +26,7 @@
 #include "splitsolve.h"
 #include "ss_internal.cuh"
 #include "ss_plan.h"
+#include "ss_tc.h"
 
 using namespace ss;
 
@@ -184,6 +185,11 @@ struct ss_handle {
   size_t dint_n = 0, ddbl_n = 0, dtr_n = 0;
   Plan p_setup, p_iter[2], p_final, p_sweep, p_bound;
   Prof prof;
+  // mixed path: packing buffer of the tensor-core GEMMs and their error flag
+  unsigned char* pack = nullptr;
+  size_t pack_bytes = 0;
+  int* tc_err = nullptr;
+  bool mixed() const { return cfg.precision != SS_FP64; }
   Prof* P() { return cfg.profile ? &prof : nullptr; }
   // cache of the last chunk
   std::vector<double> cE;
@@ -207,6 +213,15 @@ int cuda_fail(ss_handle* h, cudaError_t e, const char* where) {
     cudaError_t _e = (call);                         \
     if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
   } while (0)
+
+// A group of large GEMMs: FP64 kernel, or the split-BF16 tensor-core kernel
+// in the mixed modes.
+void big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
+  if (g.empty()) return;
+  if (!h->mixed()) { P.gemm(g); return; }
+  if (!P.tc_gemm(g, h->cfg.precision, h->pack, h->pack_bytes, h->tc_err)) h->err = "tensor-core packing buffer too small";
+}
+void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) { P.lu_solve(ds, LU_NB, h->mixed()); }
 
 // ---------------------------------------------------------- self-energies
 // Builds setup / iteration / final plans for the doubling of 2P lead problems.
@@ -298,8 +313,8 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
       }
     }
     I.form(f1);
-    I.lu_solve(lu, LU_NB);
-    I.gemm(g);
+    ::lu(h, I, lu);
+    big_gemm(h, I, g);
     I.form(f2);
     I.norm1(nr);
     I.check(na, nb, nd, act, iters, conv, NP, h->cfg.decim_tol, h->cfg.decim_max_iter, 1);
@@ -329,8 +344,8 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
     }
   }
   F.form(ff);
-  F.lu_solve(lu, LU_NB);
-  F.gemm(g);
+  ::lu(h, F, lu);
+  big_gemm(h, F, g);
 }
 
 // ------------------------------------------------------------------ sweeps
@@ -381,9 +396,9 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
         fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, W + s, ld, s, s));
       }
     }
-    S.gemm(g);
+    big_gemm(h, S, g);
     S.form(f);
-    S.lu_solve(lu, LU_NB);
+    ::lu(h, S, lu);
     S.form(fc);
   }
   // chains: Q_i = -X_i Q_{i-1} (first), P_i = -Y_i P_{i+1} (last)
@@ -403,7 +418,7 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
         fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, w.tmp[dir], s, s, s));
       }
     }
-    S.gemm(g);
+    big_gemm(h, S, g);
     S.form(fc);
   }
 }
@@ -477,11 +492,11 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
     tr.push_back({w.M1, s, w.M2, s, s, traces + p, nullptr});
   }
   B.form(f0);
-  B.gemm(gR);
+  big_gemm(h, B, gR);
   B.gemm(gb1);
   B.gemm(gb2);
   B.gemm(gsb);
-  B.lu_solve(lu, LU_NB);
+  ::lu(h, B, lu);
   B.gemm(gG1);
   B.gemm(gG2);
   B.form(fc);
@@ -807,8 +822,8 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     g_create_error = "non-positive workspace sizes";
     return SS_ERR_ARG;
   }
-  if (cfg->precision != SS_FP64) {
-    g_create_error = "precision mode not available in this build";
+  if (cfg->precision != SS_FP64 && cfg->precision != SS_MIXED_BF16X3 && cfg->precision != SS_MIXED_BF16X6) {
+    g_create_error = "unknown precision mode";
     return SS_ERR_ARG;
   }
   if (!(cfg->eta >= 0.0) || !(cfg->decim_tol >= 0.0) || cfg->decim_max_iter < 1) {
@@ -838,6 +853,25 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     if (h->own_stream) cudaStreamDestroy(h->stream);
     g_create_error = "workspace of " + std::to_string(h->arena_bytes) + " bytes: " + cudaGetErrorString(e);
     return SS_ERR_OOM;
+  }
+  if (h->mixed()) {
+    // the largest tensor-core group: the doubling products, 4 GEMMs per lead
+    // with 2 distinct A and 2 distinct B operands of s x s (B packed as 2s rows)
+    const size_t s = cfg->s_b_max;
+    const size_t kp = (size_t)tc_kp((int)s, cfg->precision);
+    const size_t per_lead = 2 * (((s * kp * 2) + 1023) & ~size_t(1023)) + 2 * (((2 * s * kp * 2) + 1023) & ~size_t(1023));
+    h->pack_bytes = (size_t)cfg->max_points * 2 * per_lead + (1 << 20);
+    e = cudaMalloc(&h->pack, h->pack_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->tc_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(h->arena);
+      cudaFree(h->pack);
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      g_create_error = "tensor-core packing buffer: " + std::string(cudaGetErrorString(e));
+      return SS_ERR_OOM;
+    }
   }
   *hp = h.release();
   return SS_OK;
@@ -977,6 +1011,8 @@ int ss_destroy(ss_handle* h) {
   for (auto& kv : h->ks) kv.second.free_all();
   h->ks.clear();
   cudaFree(h->arena);
+  cudaFree(h->pack);
+  cudaFree(h->tc_err);
   cudaFree(h->dint);
   cudaFree(h->ddbl);
   cudaFree(h->dtr);
@@ -994,6 +1030,45 @@ const char* ss_last_error(const ss_handle* h) {
 }
 
 long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
+
+int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
+             int transB, ss_c64* C, int ldc, void* stream) {
+  if (m < 0 || n < 0 || k < 1 || !A || !B || !C || lda < 1 || ldb < 1 || ldc < n ||
+      (precision != SS_FP64 && precision != SS_MIXED_BF16X3 && precision != SS_MIXED_BF16X6)) {
+    g_create_error = "ss_zgemm: bad arguments";
+    return SS_ERR_ARG;
+  }
+  if (m == 0 || n == 0) return SS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  GemmDesc g = gdesc(m, n, k, plain(reinterpret_cast<const z64*>(A), lda, transA ? 1 : 0),
+                     plain(reinterpret_cast<const z64*>(B), ldb, transB ? 1 : 0), reinterpret_cast<z64*>(C), ldc,
+                     ONE, ZERO);
+  std::vector<GemmDesc> ds(1, g);
+  Plan plan;
+  unsigned char* pack = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (precision == SS_FP64) {
+    plan.gemm(ds);
+  } else {
+    const size_t cap = Plan::tc_pack_bytes(ds, precision);
+    e = cudaMallocAsync(&pack, cap, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) { cudaGetLastError(); g_create_error = "ss_zgemm: scratch"; return SS_ERR_OOM; }
+    if (!plan.tc_gemm(ds, precision, pack, cap, err)) e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) e = plan.upload(st);
+  if (e == cudaSuccess) e = plan.run(st, nullptr);
+  int herr = 0;
+  if (err && e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (pack) cudaFreeAsync(pack, st);
+  if (err) cudaFreeAsync(err, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { g_create_error = std::string("ss_zgemm: ") + cudaGetErrorString(e); return SS_ERR_CUDA; }
+  if (herr) { g_create_error = "ss_zgemm: tensor-core pipeline wait timed out"; return SS_ERR_TIMEOUT; }
+  return SS_OK;
+}
 
 int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R, const ss_c64* G1n,
                            double* T, void* stream) {

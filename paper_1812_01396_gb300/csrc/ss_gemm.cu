@@ -40,10 +40,30 @@ __device__ __forceinline__ z64 op_load(const Operand& o, int i, int j) {
   return o.trans ? zconj(v) : v;
 }
 
+template <typename R>
+struct Cx;
+template <>
+struct Cx<double> {
+  typedef double2 T;
+  static __device__ __forceinline__ T cvt(z64 v) { return v; }
+  static __device__ __forceinline__ z64 back(T v) { return v; }
+};
+template <>
+struct Cx<float> {
+  typedef float2 T;
+  static __device__ __forceinline__ T cvt(z64 v) { return make_float2((float)v.x, (float)v.y); }
+  static __device__ __forceinline__ z64 back(T v) { return zmk((double)v.x, (double)v.y); }
+};
+
+// R = double: the FP64 kernel of the FP64 path.  R = float: operands are
+// rounded to FP32 on load and accumulated in FP32 (the low-rank LU updates of
+// the mixed path); C is still read and written in FP64.
+template <typename R>
 __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ descs,
                                                    const int* __restrict__ tile_start, int nprob) {
-  __shared__ z64 As[TK][TM];
-  __shared__ z64 Bs[TK][TN];
+  typedef typename Cx<R>::T CT;
+  __shared__ CT As[TK][TM];
+  __shared__ CT Bs[TK][TN];
   const int pid = find_problem(tile_start, nprob, blockIdx.x);
   const GemmDesc& d = descs[pid];
   if (d.active && __ldg(d.active) == 0) return;
@@ -54,29 +74,29 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const Operand a = d.a, b = d.b;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
-  z64 acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = zmk(0.0, 0.0);
+    for (int j = 0; j < 4; ++j) { acc[i][j].x = 0; acc[i][j].y = 0; }
 
   for (int k0 = 0; k0 < K; k0 += TK) {
     for (int e = tid; e < TM * TK; e += NT) {
       int r, kk;
       if (a.trans) { kk = e / TM; r = e % TM; } else { r = e / TK; kk = e % TK; }
       const int gi = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gi < m && gk < K) ? op_load(a, gi, gk) : zmk(0.0, 0.0);
+      As[kk][r] = Cx<R>::cvt((gi < m && gk < K) ? op_load(a, gi, gk) : zmk(0.0, 0.0));
     }
     for (int e = tid; e < TK * TN; e += NT) {
       int c, kk;
       if (b.trans) { c = e / TK; kk = e % TK; } else { kk = e / TN; c = e % TN; }
       const int gj = col0 + c, gk = k0 + kk;
-      Bs[kk][c] = (gj < n && gk < K) ? op_load(b, gk, gj) : zmk(0.0, 0.0);
+      Bs[kk][c] = Cx<R>::cvt((gj < n && gk < K) ? op_load(b, gk, gj) : zmk(0.0, 0.0));
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      z64 av[4], bv[4];
+      CT av[4], bv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -84,7 +104,12 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zfma(acc[i][j], av[i], bv[j]);
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(av[i].x, bv[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-av[i].y, bv[j].y, acc[i][j].x);
+          acc[i][j].y = fma(av[i].x, bv[j].y, acc[i][j].y);
+          acc[i][j].y = fma(av[i].y, bv[j].x, acc[i][j].y);
+        }
     }
     __syncthreads();
   }
@@ -99,7 +124,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
     for (int j = 0; j < 4; ++j) {
       const int c = col0 + tx + 16 * j;
       if (c >= n) continue;
-      z64 v = zmul(alpha, acc[i][j]);
+      z64 v = zmul(alpha, Cx<R>::back(acc[i][j]));
       if (d.cmode == 1) {
         const size_t fi = (size_t)r * d.ldcf + c;
         v = zadd(v, zmul(beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
@@ -122,7 +147,13 @@ int zgemm_tiles(int m, int n) {
 void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
                   cudaStream_t st) {
   if (nprob <= 0 || total_tiles <= 0) return;
-  zgemm_kernel<<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  zgemm_kernel<double><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+}
+
+void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
+                    cudaStream_t st) {
+  if (nprob <= 0 || total_tiles <= 0) return;
+  zgemm_kernel<float><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
 }
 
 }  // namespace ss

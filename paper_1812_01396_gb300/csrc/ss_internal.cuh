@@ -111,6 +111,10 @@ struct TraceDesc {  // out = sum_{a,b} A[a,b] * B[b,a]
 void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
                   cudaStream_t st);
 int zgemm_tiles(int m, int n);  // CTAs one problem needs
+// Same descriptors, FP32 arithmetic (operands rounded to FP32 on load, FP32
+// accumulation, FP64 C): the low-rank LU updates of the mixed path.
+void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
+                    cudaStream_t st);
 
 void launch_zform(const FormDesc* d, const int* tile_start, int nprob, int total_tiles,
                   cudaStream_t st);

@@ -2,10 +2,123 @@
 #include "ss_plan.h"
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 
 namespace ss {
 
-void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb) {
+namespace {
+struct OpKey {
+  const void* p; const void* s; double er, ei; int ld, trans, rows, k, role;
+  bool operator<(const OpKey& o) const {
+    return std::tie(p, s, er, ei, ld, trans, rows, k, role) <
+           std::tie(o.p, o.s, o.er, o.ei, o.ld, o.trans, o.rows, o.k, o.role);
+  }
+};
+size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
+}  // namespace
+
+size_t Plan::tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode) {
+  std::map<OpKey, int> seen;
+  size_t tot = 0;
+  for (auto& g : ds) {
+    const int kp = tc_kp(g.k, mode);
+    OpKey ka{g.a.p, g.a.s, g.a.e.x, g.a.e.y, g.a.ld, g.a.trans, g.m, g.k, 0};
+    OpKey kb{g.b.p, g.b.s, g.b.e.x, g.b.e.y, g.b.ld, g.b.trans, 2 * g.n, g.k, 1};
+    if (!seen.count(ka)) { seen[ka] = 1; tot += al1k((size_t)g.m * kp * 2); }
+    if (!seen.count(kb)) { seen[kb] = 1; tot += al1k((size_t)2 * g.n * kp * 2); }
+  }
+  return tot;
+}
+
+bool Plan::tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pack, size_t cap, int* err) {
+  if (ds.empty()) return true;
+  std::map<OpKey, int> index;   // operand -> position in pa / pb
+  std::vector<PackDesc> pa, pb;
+  std::vector<CUtensorMap> maps;
+  std::vector<int> map_of_a, map_of_b;
+  std::vector<int> amap(ds.size()), bmap(ds.size());
+  size_t used = 0;
+  for (size_t i = 0; i < ds.size(); ++i) {
+    const GemmDesc& g = ds[i];
+    const int kp = tc_kp(g.k, mode);
+    for (int role = 0; role < 2; ++role) {
+      const Operand& o = role == 0 ? g.a : g.b;
+      const int rows = role == 0 ? g.m : 2 * g.n;
+      OpKey key{o.p, o.s, o.e.x, o.e.y, o.ld, o.trans, rows, g.k, role};
+      auto it = index.find(key);
+      int mi;
+      if (it == index.end()) {
+        const size_t bytes = al1k((size_t)rows * kp * 2);
+        if (used + bytes > cap) return false;
+        PackDesc d{};
+        d.x = o.p; d.s = o.s; d.e = o.e; d.ld = o.ld; d.trans = o.trans;
+        d.rows = rows; d.k = g.k; d.kp = kp;
+        d.out = reinterpret_cast<__nv_bfloat16*>(pack + used);
+        d.active = g.active;
+        CUtensorMap m;
+        if (encode_kmajor_map(&m, pack + used, rows, kp, role == 0 ? tc_box_rows_a() : tc_box_rows_b()) !=
+            cudaSuccess)
+          return false;
+        used += bytes;
+        mi = (int)maps.size();
+        maps.push_back(m);
+        (role == 0 ? pa : pb).push_back(d);
+        index[key] = mi;
+      } else {
+        mi = it->second;
+      }
+      (role == 0 ? amap : bmap)[i] = mi;
+    }
+  }
+  // pack launches
+  for (int role = 0; role < 2; ++role) {
+    std::vector<PackDesc>& v = role == 0 ? pa : pb;
+    std::vector<int> start(v.size());
+    int tot = 0;
+    for (size_t i = 0; i < v.size(); ++i) { start[i] = tot; tot += pack_tiles(v[i].rows, v[i].kp); }
+    LaunchRec r;
+    r.kind = role == 0 ? K_PACK_A : K_PACK_B;
+    r.off = push_vec(v);
+    r.toff = push_vec(start);
+    r.nprob = (int)v.size();
+    r.tiles = tot;
+    r.ival = mode;
+    recs_.push_back(r);
+  }
+  // GEMM descriptors followed by their tensor maps (64-byte aligned)
+  std::vector<TcDesc> tds(ds.size());
+  std::vector<int> start(ds.size());
+  int tot = 0;
+  for (size_t i = 0; i < ds.size(); ++i) {
+    const GemmDesc& g = ds[i];
+    TcDesc t{};
+    t.m = g.m; t.n2 = 2 * g.n; t.kp = tc_kp(g.k, mode); t.kc = g.k;
+    t.c = g.c; t.ldc = g.ldc; t.cmode = g.cmode; t.alpha = g.alpha; t.beta = g.beta;
+    t.cs = g.cs; t.ch = g.ch; t.ce = g.ce; t.ldcf = g.ldcf; t.active = g.active;
+    tds[i] = t;
+    start[i] = tot;
+    tot += tc_tiles(t.m, t.n2);
+  }
+  const size_t doff = push(nullptr, tds.size() * sizeof(TcDesc), 64);
+  const size_t moff = push_vec(maps, 64);
+  for (size_t i = 0; i < ds.size(); ++i) {
+    tds[i].ta_off = (long long)(moff + (size_t)amap[i] * sizeof(CUtensorMap) - doff);
+    tds[i].tb_off = (long long)(moff + (size_t)bmap[i] * sizeof(CUtensorMap) - doff);
+  }
+  std::memcpy(host_.data() + doff, tds.data(), tds.size() * sizeof(TcDesc));
+  LaunchRec r;
+  r.kind = K_TCGEMM;
+  r.off = doff;
+  r.toff = push_vec(start);
+  r.nprob = (int)ds.size();
+  r.tiles = tot;
+  r.p[0] = err;
+  recs_.push_back(r);
+  return true;
+}
+
+void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates) {
   if (ds.empty()) return;
   const size_t off = push_vec(ds);
   const int np = (int)ds.size();
@@ -39,7 +152,7 @@ void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb) {
     rr.kind = K_LU_ROW;
     rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.maxc = maxc;
     recs_.push_back(rr);
-    gemm(g);
+    gemm(g, fp32_updates);
   }
   // backward substitution on the right-hand sides: panels right to left
   int maxrhs = 0;
@@ -65,7 +178,7 @@ void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb) {
       q.active = d.active;
       g.push_back(q);
     }
-    gemm(g);
+    gemm(g, fp32_updates);
   }
 }
 
@@ -101,15 +214,23 @@ cudaError_t Plan::upload(cudaStream_t st) {
   return cudaMemcpyAsync(dev_, host_.data(), host_.size(), cudaMemcpyHostToDevice, st);
 }
 
+static bool prof_active(const int* a, const Prof* prof) {
+  if (!a || !prof->act_host) return true;
+  const long idx = a - prof->act_dev;
+  return !(idx >= 0 && idx < prof->nact && !prof->act_host[idx]);
+}
+
 static double gemm_flops(const LaunchRec& r, const std::vector<unsigned char>& host, const Prof* prof) {
-  const GemmDesc* g = reinterpret_cast<const GemmDesc*>(host.data() + r.off);
   double f = 0.0;
-  for (int i = 0; i < r.nprob; ++i) {
-    if (g[i].active && prof->act_host) {
-      const long idx = g[i].active - prof->act_dev;
-      if (idx >= 0 && idx < prof->nact && !prof->act_host[idx]) continue;
-    }
-    f += 8.0 * g[i].m * (double)g[i].n * g[i].k;
+  if (r.kind == K_GEMM || r.kind == K_GEMM32) {
+    const GemmDesc* g = reinterpret_cast<const GemmDesc*>(host.data() + r.off);
+    for (int i = 0; i < r.nprob; ++i)
+      if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)g[i].n * g[i].k;
+  } else if (r.kind == K_TCGEMM) {
+    // algorithmic complex flops (8 m n k), not the split-term tensor flops
+    const TcDesc* g = reinterpret_cast<const TcDesc*>(host.data() + r.off);
+    for (int i = 0; i < r.nprob; ++i)
+      if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)(g[i].n2 / 2) * (double)g[i].kc;
   }
   return f;
 }
@@ -120,7 +241,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     Prof::Rec pr{};
     if (prof && r.kind != K_MEMSET) {
       pr.kind = r.kind;
-      pr.flops = r.kind == K_GEMM ? gemm_flops(r, host_, prof) : 0.0;
+      pr.flops = (r.kind == K_GEMM || r.kind == K_TCGEMM || r.kind == K_GEMM32) ? gemm_flops(r, host_, prof) : 0.0;
       cudaEventCreate(&pr.a);
       cudaEventCreate(&pr.b);
       cudaEventRecord(pr.a, st);
@@ -129,6 +250,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     const int* t = reinterpret_cast<const int*>(dev_ + r.toff);
     switch (r.kind) {
       case K_GEMM: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_GEMM32: launch_zgemm32((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_LU_ROW:
@@ -143,6 +265,14 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
         ++n;
         break;
       case K_FILL: launch_fill_i32((int*)r.p[0], r.nprob, r.ival, st); ++n; break;
+      case K_PACK_A: launch_pack_a((const PackDesc*)d, t, r.nprob, r.tiles, r.ival, st); ++n; break;
+      case K_PACK_B: launch_pack_b((const PackDesc*)d, t, r.nprob, r.tiles, r.ival, st); ++n; break;
+      case K_TCGEMM: {
+        cudaError_t e = launch_tc_gemm((const TcDesc*)d, t, r.nprob, r.tiles, (int*)r.p[0], st);
+        if (e != cudaSuccess) return e;
+        ++n;
+        break;
+      }
       case K_MEMSET: {
         cudaError_t e = cudaMemsetAsync(r.p[0], 0, r.bytes, st);
         if (e != cudaSuccess) return e;

@@ -9,12 +9,13 @@
 #include <vector>
 
 #include "ss_internal.cuh"
+#include "ss_tc.h"
 
 namespace ss {
 
 // Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
 enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
-                  K_FILL, K_MEMSET };
+                  K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_MEMSET };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -65,23 +66,25 @@ class Plan {
     recs_.clear();
     destroy_graph();
   }
-  size_t push(const void* data, size_t bytes) {
-    size_t off = (host_.size() + 15) & ~size_t(15);
+  size_t push(const void* data, size_t bytes, size_t align = 16) {
+    size_t off = (host_.size() + align - 1) & ~(align - 1);
     host_.resize(off + bytes);
-    if (bytes) std::memcpy(host_.data() + off, data, bytes);
+    if (bytes && data) std::memcpy(host_.data() + off, data, bytes);
+    else if (bytes) std::memset(host_.data() + off, 0, bytes);
     return off;
   }
   template <class D>
-  size_t push_vec(const std::vector<D>& v) { return push(v.data(), v.size() * sizeof(D)); }
+  size_t push_vec(const std::vector<D>& v, size_t align = 16) { return push(v.data(), v.size() * sizeof(D), align); }
 
-  void gemm(const std::vector<GemmDesc>& ds) {
+  // fp32 = true: the FP32-arithmetic kernel (low-rank updates of the mixed path)
+  void gemm(const std::vector<GemmDesc>& ds, bool fp32 = false) {
     if (ds.empty()) return;
     std::vector<int> start(ds.size());
     int tot = 0;
     for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zgemm_tiles(ds[i].m, ds[i].n); }
     if (tot == 0) return;
     LaunchRec r;
-    r.kind = K_GEMM;
+    r.kind = fp32 ? K_GEMM32 : K_GEMM;
     r.off = push_vec(ds);
     r.toff = push_vec(start);
     r.nprob = (int)ds.size();
@@ -102,9 +105,18 @@ class Plan {
     r.tiles = tot;
     recs_.push_back(r);
   }
+  // Complex GEMMs on the tensor cores (split-BF16, mode 1: 3 products,
+  // mode 2: 6 products).  Operands are packed into the device buffer `pack`
+  // (cap bytes, reused by every tc_gemm group of the plan: launches are
+  // stream-ordered); identical operands of the group are packed once.
+  // Returns false if the packed operands do not fit or a tensor map fails.
+  bool tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pack, size_t cap, int* err);
+  static size_t tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode);
   // Blocked LU + solve of every problem in ds (panel width nb <= 32; nb <= 0
   // picks the width from the largest block of the group).
-  void lu_solve(const std::vector<LuDesc>& ds, int nb);
+  // fp32_updates: rank-nb trailing and back-substitution updates in FP32
+  // arithmetic (panels, pivots and triangular blocks stay FP64).
+  void lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates = false);
   void norm1(const std::vector<Norm1Desc>& ds) {
     if (ds.empty()) return;
     LaunchRec r;

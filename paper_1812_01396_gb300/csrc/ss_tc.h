@@ -1,0 +1,55 @@
+// Tensor-core (tcgen05) complex GEMM: descriptors and launchers.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+// Packing of one complex operand into split-BF16 real form (see ss_tc.cu).
+// For A: rows = m, element (i, kk) of op(X) for i < m, kk < k.
+// For B: rows = 2n, element (kk, j) of op(X) for kk < k, j < n.
+struct PackDesc {
+  const z64* x;     // plain matrix, or H of a formed operand
+  const z64* s;     // S of a formed operand (e*S - H), else null
+  z64 e;
+  int ld, trans;
+  int rows, k, kp;  // packed matrix is rows x kp, row-major BF16
+  __nv_bfloat16* out;
+  const int* active;
+};
+
+// One real GEMM C' = A' B'^T (m x n2, n2 = 2n) with the complex epilogue
+// C = alpha (C're + i C'im) + beta Cin (cmode as in GemmDesc).
+struct TcDesc {
+  long long ta_off;  // byte offsets of the two 64-byte aligned tensor maps,
+  long long tb_off;  // relative to the start of the TcDesc array
+  int m, n2, kp;
+  int kc;  // complex inner dimension (for the algorithmic flop count)
+  z64* c;
+  int ldc;
+  int cmode;
+  z64 alpha, beta;
+  const z64* cs;
+  const z64* ch;
+  z64 ce;
+  int ldcf;
+  const int* active;
+};
+
+int tc_kp(int k, int mode);           // padded packed K for mode 1 (3 products) / 2 (6 products)
+int tc_tiles(int m, int n2);
+int pack_tiles(int rows, int kp);
+size_t tc_smem_bytes();
+int tc_box_rows_a();
+int tc_box_rows_b();
+cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int kp, int box_rows);
+
+void launch_pack_a(const PackDesc* d, const int* tile_start, int nprob, int total, int mode, cudaStream_t st);
+void launch_pack_b(const PackDesc* d, const int* tile_start, int nprob, int total, int mode, cudaStream_t st);
+cudaError_t launch_tc_gemm(const TcDesc* d, const int* tile_start, int nprob, int total, int* err,
+                           cudaStream_t st);
+
+}  // namespace ss

@@ -291,7 +291,8 @@ def test_caroli_transmission_entry_point(ss):
     import torch
     pts = [(synth.make_device(4, 40, seed=20)[0], 0.3), (synth.make_device(4, 40, seed=21)[0], -0.5)]
     refs = [dense.solve_point(d, E) for d, E in pts]
-    t = lambda key: torch.from_numpy(np.stack([r[key] for r in refs])).cuda()
+    # the oracle's blocks may be Fortran-ordered views: pass dense row-major copies
+    t = lambda key: torch.from_numpy(np.ascontiguousarray(np.stack([r[key] for r in refs]))).cuda()
     T = torch.zeros(2, dtype=torch.float64, device="cuda")
     ss.ss_caroli_transmission(t("sigma_L"), t("sigma_R"), t("G1n"), T)
     for p, r in enumerate(refs):
