@@ -167,6 +167,24 @@ int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int t
 int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R,
                            const ss_c64* G1n, double* T, void* stream);
 
+/* Allocation-free variant of ss_caroli_transmission (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory, e.g.
+ * code running under a pool allocator that owns the device, or a hook that
+ * must not call cudaMalloc / cudaMallocAsync while another allocator is
+ * active).  Same arguments and result as ss_caroli_transmission, but all
+ * scratch comes from one fixed file-scope device array of about 4.6 MB that
+ * every GPU loading the library holds until the process exits; the call
+ * allocates nothing.  Limits: n_pts <= 256 and n_pts*s_b*s_b <= 65536,
+ * larger problems are rejected with SS_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Every call reuses the same array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  No part of the array needs to start at zero.
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA; message in ss_noalloc_last_error(). */
+int ss_caroli_transmission_noalloc(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R,
+                                   const ss_c64* G1n, double* T, void* stream);
+const char* ss_noalloc_last_error(void);
+
 /* Kernel kinds for ss_profile_read. */
 #define SS_KERNEL_ZGEMM      0  /* batched complex GEMM (all GEMM-shaped steps)      */
 #define SS_KERNEL_FORM       1  /* elementwise forms / copies                         */

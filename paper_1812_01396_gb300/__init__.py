@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGU
 
 EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
            "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
-           "ss_profile_reset", "ss_zgemm", "ss_caroli_transmission")
+           "ss_profile_reset", "ss_zgemm", "ss_caroli_transmission",
+           "ss_caroli_transmission_noalloc", "ss_noalloc_last_error")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6}
 
 
@@ -81,6 +82,10 @@ def load_library(path: str = LIB_PATH):
     lib.ss_zgemm.restype = C.c_int
     lib.ss_caroli_transmission.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.ss_caroli_transmission.restype = C.c_int
+    lib.ss_caroli_transmission_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
+    lib.ss_caroli_transmission_noalloc.restype = C.c_int
+    lib.ss_noalloc_last_error.argtypes = []
+    lib.ss_noalloc_last_error.restype = C.c_char_p
     for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
                  "ss_destroy"):
         getattr(lib, name).restype = C.c_int
@@ -303,3 +308,17 @@ def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):
     if rc != SS_OK:
         raise SSError(rc, lib.ss_last_error(None).decode())
 
+def ss_caroli_transmission_noalloc(sigma_L, sigma_R, G1n, T, stream=None):
+    """Allocation-free Caroli transmission (scratch in a fixed device array).
+
+    For callers that cannot allocate device memory; same result as
+    :func:`ss_caroli_transmission`.  Limits: P <= 256, P*s^2 <= 65536.
+    Inputs must already be contiguous: copying them would allocate."""
+    lib = load_library()
+    for t in (sigma_L, sigma_R, G1n, T):
+        if not t.is_contiguous():
+            raise ValueError("inputs and outputs must be contiguous (dense row-major)")
+    P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
+    rc = lib.ss_caroli_transmission_noalloc(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
+    if rc != SS_OK:
+        raise SSError(rc, lib.ss_noalloc_last_error().decode())
