@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--n_b", type=int, default=64)
     ap.add_argument("--s_b", type=int, default=512)
     ap.add_argument("--n_inj", type=int, default=32)
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -206,107 +207,137 @@ def main():
         if world > 1:
             dist.barrier()
 
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        tt = torch.tensor([v], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
     devs, pts = workload(a)
     stream = torch.cuda.Stream()
     P = a.batch
-    h = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=1,
-                  stream=stream.cuda_stream)
-    tdev = []
     with torch.cuda.stream(stream):
-        for k, d in enumerate(devs):
-            t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to("cuda", non_blocking=False)
-            h.set_hamiltonian(k, t(d.H_diag), t(d.H_up), t(d.S_diag), t(d.S_up))
+        tdevs = [tuple(torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (d.H_diag, d.H_up, d.S_diag, d.S_up))
+                 for d in devs]
         inj_host = synth.make_injection(a.s_b, a.n_inj, seed=2, n_pts=P)
         inj_dev = torch.from_numpy(inj_host).cuda()
     stream.synchronize()
-
-    # this rank's points: a strided slice of the grid, P per step
-    mine = pts[rank::world]
+    mine = pts[rank::world]   # this rank's points: a strided slice of the grid
 
     def batch(step):
         sel = [mine[(step * P + i) % len(mine)] for i in range(P)]
         return [e for e, _ in sel], [k for _, k in sel]
+
+    def handle(prec, device_ptrs=1, profile=0):
+        h = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=device_ptrs,
+                      stream=stream.cuda_stream, precision=prec, profile=profile)
+        with torch.cuda.stream(stream):
+            for k, d in enumerate(devs):
+                if device_ptrs:
+                    h.set_hamiltonian(k, *tdevs[k])
+                else:
+                    h.set_device(k, d)
+        stream.synchronize()
+        return h
 
     def step(hh, s, inj, want_x=True):
         E, K = batch(s)
         _, _, it, st0, _ = hh.self_energy(E, K)
         xs, st1, _ = hh.solve(E, K, inj, want_x=want_x)
         T, err, st2, _ = hh.transmission(E, K)
-        return it, T, np.maximum(np.maximum(st0, st1), st2)
+        Tn = T.cpu().numpy() if hasattr(T, "cpu") else np.asarray(T)
+        return it, Tn, np.maximum(np.maximum(st0, st1), st2)
 
-    with torch.cuda.stream(stream):
-        for s in range(a.warmup):
-            step(h, s, inj_dev)
-    stream.synchronize()
+    def measure(prec, steps, warmup, clocks=None, start=None):
+        """Timed region on device-resident inputs (steps start..start+steps-1 of the
+        point grid), then a profiled pass of the same steps."""
+        start = warmup if start is None else start
+        h = handle(prec)
+        with torch.cuda.stream(stream):
+            for s_ in range(warmup):
+                step(h, s_, inj_dev)
+        stream.synchronize()
+        launches0 = h.launch_count()
+        iters, Ts, sts = [], [], []
+        barrier()
+        torch.cuda.synchronize()
+        ctx = clocks if clocks is not None else _Null()
+        with ctx:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for s_ in range(start, start + steps):
+                    it, T, st = step(h, s_, inj_dev)
+                    iters.append(it)
+                    Ts.append(T)
+                    sts.append(st)
+            e1.record(stream)
+            e1.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        t = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+        launches = h.launch_count() - launches0
+        h.close()
+        flops = sum(point_flops(a.n_b, a.s_b, a.n_inj, int(it[p, 0]), int(it[p, 1])) for it in iters for p in range(P))
+        hp = handle(prec, profile=1)
+        with torch.cuda.stream(stream):
+            step(hp, 0, inj_dev)
+            hp.profile_reset()
+            for s_ in range(start, start + steps):
+                step(hp, s_, inj_dev)
+        stream.synchronize()
+        kern = {}
+        for name in ss.KERNEL_KINDS:
+            ms, fl, n = hp.profile_read(name)
+            kern[name] = {"ms": ms, "launches": n, "flops": fl, "issued": hp.profile_issued(name)}
+        hp.close()
+        return dict(t=t, value=P * steps * world / t, tflops=flops * world / t / 1e12, kern=kern, launches=launches,
+                    T=np.concatenate(Ts), ok=bool(np.all(np.concatenate(sts) == 0)), steps=steps)
 
-    # ---- timed region (device-resident inputs)
-    launches0 = h.launch_count()
-    flops = 0.0
-    iters = []
+    run_mixed = a.precision in ("mixed", "both")
+    run_fp64 = a.precision in ("fp64", "both")
     clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                               f"clocks_rank{rank}.csv"))
-    barrier()
-    torch.cuda.synchronize()
-    with clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        with torch.cuda.stream(stream):
-            for s in range(a.warmup, a.warmup + a.steps):
-                it, T, st = step(h, s, inj_dev)
-                iters.append(it)
-        e1.record(stream)
-        e1.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    t_dev = e0.elapsed_time(e1) * 1e-3
-    launches = h.launch_count() - launches0
-    for it in iters:
-        for p in range(P):
-            flops += point_flops(a.n_b, a.s_b, a.n_inj, int(it[p, 0]), int(it[p, 1]))
-    t_max = t_dev
-    if world > 1:
-        tt = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    n_solved = P * a.steps * world
-    value = n_solved / t_max
+    head_prec = ss.SS_MIXED_OZAKI if run_mixed else ss.SS_FP64
+    head = measure(head_prec, a.steps, a.warmup, clk)
+    other = None
+    if run_mixed and run_fp64:
+        # the plain FP64 path on the same points (fewer steps: ~9 s per step)
+        other = measure(ss.SS_FP64, min(a.steps, 2), 1, start=a.warmup)
 
-    # ---- profiled pass (same steps): per-kernel device time with CUDA events
-    hp = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=1,
-                   stream=stream.cuda_stream, profile=1)
-    with torch.cuda.stream(stream):
-        for k, d in enumerate(devs):
-            t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
-            hp.set_hamiltonian(k, t(d.H_diag), t(d.H_up), t(d.S_diag), t(d.S_up))
-        step(hp, 0, inj_dev)
-        hp.profile_reset()
-        for s in range(a.warmup, a.warmup + a.steps):
-            step(hp, s, inj_dev)
-    stream.synchronize()
-    kern = {}
-    for name in ss.KERNEL_KINDS:
-        ms, fl, n = hp.profile_read(name)
-        kern[name] = {"ms": ms, "launches": n, "flops": fl}
-    hp.close()
+    # live roofline of the dominant kernel: the exact tensor-core GEMM (mixed)
+    # or the FP64 complex GEMM
+    peak_fp64 = fp64_gemm_peak(torch)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    kern = head["kern"]
     tot_ms = sum(v["ms"] for v in kern.values()) or 1.0
-    g = kern["zgemm"]
-    peak_meas = fp64_gemm_peak(torch)
-    achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
-                "frac": achieved / peak_meas if peak_meas else None, "traffic": None,
-                "kernel": "zgemm_kernel (FP64 DFMA complex GEMM)",
-                "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64 pipe); nominal 1.25",
-                "avg_launch_ms": g["ms"] / max(g["launches"], 1),
-                "share_of_kernel_time": g["ms"] / tot_ms}
+    if head_prec == ss.SS_FP64:
+        g = kern["zgemm"]
+        achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                    "frac": achieved / peak_fp64, "traffic": None, "kernel": "zgemm_kernel (FP64 DFMA complex GEMM)",
+                    "peak_source": "measured cuBLAS DGEMM 8192^3 in this run (FP64 pipe)",
+                    "avg_launch_ms": g["ms"] / max(g["launches"], 1), "share_of_kernel_time": g["ms"] / tot_ms}
+    else:
+        g = kern["ozgemm"]
+        ms = g["ms"]
+        # tensor-pipe flops actually issued (digit pairs x padded slice width)
+        alg = g["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        tensor = g["issued"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        pk = peaks.get("bf16_tflops_sustained") or 1700.0
+        roofline = {"bound": "tensor", "achieved": tensor, "peak": pk, "unit": "TFLOP/s", "frac": tensor / pk,
+                    "traffic": None, "kernel": "oz_gemm_kernel (digit-sliced BF16 tcgen05, exact FP32 accumulation)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                    "algorithmic_complex_fp64_equiv_tflops": alg,
+                    "avg_launch_ms": ms / max(g["launches"], 1), "share_of_kernel_time": ms / tot_ms}
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region
+    # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
     if not a.no_e2e:
-        he = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=0,
-                       stream=stream.cuda_stream)
-        for k, d in enumerate(devs):
-            he.set_device(k, d)
+        he = handle(head_prec, device_ptrs=0)
         pinned = torch.from_numpy(inj_host).pin_memory().numpy()
         inj_list = [pinned[i] for i in range(P)]
         with torch.cuda.stream(stream):
@@ -315,45 +346,59 @@ def main():
         barrier()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for s in range(a.warmup, a.warmup + a.steps):
-                step(he, s, inj_list)
+            for s_ in range(a.warmup, a.warmup + a.steps):
+                step(he, s_, inj_list)
         stream.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0)
         he.close()
-        h2d = P * 2 * a.s_b * a.n_inj * 16
-        d2h = P * a.n_b * a.s_b * a.n_inj * 16 + P * 8
-        e2e = {"value": n_solved / te, "unit": "(E,k) solves/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+        e2e = {"value": P * a.steps * world / te, "unit": "(E,k) solves/s",
+               "h2d_bytes_per_step": P * 2 * a.s_b * a.n_inj * 16,
+               "d2h_bytes_per_step": P * a.n_b * a.s_b * a.n_inj * 16 + P * 8}
 
     if rank == 0:
         cpu = None
         if not a.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(devs, pts, inj_host[0])
+        cmp = None
+        if other is not None:
+            nT = len(other["T"])
+            terr = [abs(x - y) / max(1.0, abs(y)) for x, y in zip(head["T"][:nT], other["T"])]
+            cmp = {"fp64_path": {"value": other["value"], "tflops": other["tflops"], "ms_per_step": 1e3 * other["t"] / other["steps"],
+                                 "kernels_ms": {k: round(v["ms"], 3) for k, v in other["kern"].items()}},
+                   "speedup_mixed_over_fp64": head["value"] / other["value"],
+                   "max_rel_T_err_mixed_vs_fp64": max(terr), "points_compared": nT}
         line = {
-            "metric": METRIC, "value": value, "unit": "(E,k) solves/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": "(E,k) solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * head["t"] / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head_prec == ss.SS_FP64 else "bf16 digit slices, exact fp32 accum -> f64",
+            "data": "synthetic",
             "config": {"workload": wl_name(a), "n_b": a.n_b, "s_b": a.s_b, "points_per_step": P,
-                       "n_inj": a.n_inj, "precision": "fp64", "parallelism": f"(E,k) shards x{world}",
+                       "n_inj": a.n_inj, "precision": "fp64" if head_prec == ss.SS_FP64 else "mixed (SS_MIXED_OZAKI)",
+                       "parallelism": f"(E,k) shards x{world}",
                        "l2": "inputs larger than L2: per-step workspace "
                              f"{P * (2 * a.n_b + 43) * a.s_b ** 2 * 16 / 1e9:.1f} GB"},
-            "tflops": flops * world / t_max / 1e12,
+            "tflops": head["tflops"],
             "roofline": roofline,
             "kernels_ms": {k: round(v["ms"], 3) for k, v in kern.items()},
+            "mixed_vs_fp64": cmp,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches,
+            "gpu_launches": head["launches"],
             "clocks": clk.summary(),
-            "status_ok": bool(np.all(st == 0)),
+            "status_ok": head["ok"],
         }
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
 if __name__ == "__main__":

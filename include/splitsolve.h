@@ -59,6 +59,9 @@ typedef struct ss_handle ss_handle;
                                FP32 accumulation; FP64 panels, boundary, residual and
                                iterative refinement                                     */
 #define SS_MIXED_BF16X6  2  /* as above with a 3-term BF16 split (6 products)          */
+#define SS_MIXED_OZAKI   3  /* products on tcgen05 tensor cores from BF16 digit slices with
+                               exact FP32 accumulation (FP64-accurate); FP64 panels,
+                               pivoting, boundary solve and residual                     */
 
 typedef struct {
   int n_b_max;        /* largest n_b of any k_id (workspace sizing)                   */
@@ -148,8 +151,9 @@ long long ss_launch_count(const ss_handle* h);
  * conjugate transpose (transA / transB = 1), all DEVICE pointers, row-major
  * with leading dimensions lda, ldb, ldc (elements).  precision SS_FP64 runs
  * the FP64 kernel of the FP64 path; SS_MIXED_BF16X3 / X6 run the split-BF16
- * tcgen05 kernel of the mixed path (packing scratch allocated with
- * cudaMallocAsync on `stream`).  The call synchronises `stream`.
+ * tcgen05 kernel (about 5e-6 relative error); SS_MIXED_OZAKI runs the
+ * digit-sliced tcgen05 kernel (FP64-accurate).  Packing scratch is allocated
+ * with cudaMallocAsync on `stream`.  The call synchronises `stream`.
  * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_TIMEOUT (a bounded
  * pipeline wait inside the tensor-core kernel expired). */
 int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
@@ -193,12 +197,24 @@ const char* ss_noalloc_last_error(void);
 #define SS_KERNEL_LU_BACK    4  /* backward substitution in a diagonal block of U     */
 #define SS_KERNEL_NORM1      5  /* matrix 1-norms of the doubling test                */
 #define SS_KERNEL_TRACE      6  /* transmission trace                                 */
+#define SS_KERNEL_CHECK      7  /* doubling convergence flags                         */
+#define SS_KERNEL_FILL       8  /* flag initialisation                                */
+#define SS_KERNEL_TC_PACK_A  9  /* split-BF16 packing of A (3/6-product modes)        */
+#define SS_KERNEL_TC_PACK_B 10  /* split-BF16 packing of B                            */
+#define SS_KERNEL_TCGEMM    11  /* split-BF16 tcgen05 GEMM                            */
+#define SS_KERNEL_ZGEMM32   12  /* FP32-arithmetic complex GEMM                       */
+#define SS_KERNEL_OZ_SCALE  13  /* row/column power-of-two scales of the exact GEMM   */
+#define SS_KERNEL_OZ_PACK   14  /* BF16 digit slices of the exact GEMM                */
+#define SS_KERNEL_OZGEMM    15  /* digit-sliced tcgen05 GEMM, exact FP32 accumulation */
 
 /* With cfg.profile = 1: total device time (ms, CUDA events around each
  * launch on cfg.stream), algorithmic flops (GEMM kind only: 8 m n k per
- * complex product of every active problem) and launch count of one kernel
+ * complex product of every active problem, for every GEMM kind) and launch count of one kernel
  * kind since ss_create or the last ss_profile_reset.  Errors: SS_ERR_ARG. */
 int ss_profile_read(ss_handle* h, int kind, double* total_ms, double* flops, long long* launches);
+/* Flops the tensor pipe executed for kind SS_KERNEL_OZGEMM (2 * m * 2n *
+ * digit pairs * padded slice width per product), for roofline fractions. */
+int ss_profile_read_issued(ss_handle* h, int kind, double* issued_flops);
 int ss_profile_reset(ss_handle* h);
 
 #ifdef __cplusplus

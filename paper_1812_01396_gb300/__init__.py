@@ -22,15 +22,17 @@ LIB_PATH = os.path.join(HERE, "libsplitsolve.so")
 
 SS_OK, SS_ERR_ARG, SS_ERR_STATE, SS_ERR_SINGULAR, SS_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 SS_ERR_TIMEOUT, SS_ERR_OOM, SS_ERR_CUDA = 5, 6, 7
-SS_FP64, SS_MIXED_BF16X3, SS_MIXED_BF16X6 = 0, 1, 2
+SS_FP64, SS_MIXED_BF16X3, SS_MIXED_BF16X6, SS_MIXED_OZAKI = 0, 1, 2, 3
 STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGULAR",
                 4: "SS_ERR_NOT_CONVERGED", 5: "SS_ERR_TIMEOUT", 6: "SS_ERR_OOM", 7: "SS_ERR_CUDA"}
 
 EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
            "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
-           "ss_profile_reset", "ss_zgemm", "ss_caroli_transmission",
+           "ss_profile_reset", "ss_profile_read_issued", "ss_zgemm", "ss_caroli_transmission",
            "ss_caroli_transmission_noalloc", "ss_noalloc_last_error")
-KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6}
+KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
+                "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
+                "oz_scale": 13, "oz_pack": 14, "ozgemm": 15}
 
 
 class SSConfig(C.Structure):
@@ -75,6 +77,8 @@ def load_library(path: str = LIB_PATH):
     lib.ss_launch_count.restype = C.c_longlong
     lib.ss_profile_read.argtypes = [vp, C.c_int, dp, dp, C.POINTER(C.c_longlong)]
     lib.ss_profile_read.restype = C.c_int
+    lib.ss_profile_read_issued.argtypes = [vp, C.c_int, dp]
+    lib.ss_profile_read_issued.restype = C.c_int
     lib.ss_profile_reset.argtypes = [vp]
     lib.ss_profile_reset.restype = C.c_int
     lib.ss_zgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp,
@@ -167,6 +171,13 @@ class Handle:
         k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
         self._check(self._lib.ss_profile_read(self._h, k, C.byref(ms), C.byref(fl), C.byref(n)))
         return ms.value, fl.value, n.value
+
+    def profile_issued(self, kind):
+        """Tensor-pipe flops issued by a kernel kind (needs profile=1)."""
+        v = C.c_double()
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        self._check(self._lib.ss_profile_read_issued(self._h, k, C.byref(v)))
+        return v.value
 
     def profile_reset(self):
         self._check(self._lib.ss_profile_reset(self._h))
@@ -307,6 +318,7 @@ def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):
     rc = lib.ss_caroli_transmission(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
     if rc != SS_OK:
         raise SSError(rc, lib.ss_last_error(None).decode())
+
 
 def ss_caroli_transmission_noalloc(sigma_L, sigma_R, G1n, T, stream=None):
     """Allocation-free Caroli transmission (scratch in a fixed device array).

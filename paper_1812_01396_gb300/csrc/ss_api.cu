@@ -190,6 +190,7 @@ struct ss_handle {
   size_t pack_bytes = 0;
   int* tc_err = nullptr;
   bool mixed() const { return cfg.precision != SS_FP64; }
+  bool plan_error = false;  // a tensor-core group did not fit the packing buffer
   Prof* P() { return cfg.profile ? &prof : nullptr; }
   // cache of the last chunk
   std::vector<double> cE;
@@ -216,12 +217,21 @@ int cuda_fail(ss_handle* h, cudaError_t e, const char* where) {
 
 // A group of large GEMMs: FP64 kernel, or the split-BF16 tensor-core kernel
 // in the mixed modes.
-void big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
-  if (g.empty()) return;
-  if (!h->mixed()) { P.gemm(g); return; }
-  if (!P.tc_gemm(g, h->cfg.precision, h->pack, h->pack_bytes, h->tc_err)) h->err = "tensor-core packing buffer too small";
+// A group of large GEMMs: the FP64 kernel, or in the mixed mode the
+// FP64-accurate digit-sliced kernel on the tensor cores.
+bool big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
+  if (g.empty()) return true;
+  if (!h->mixed()) { P.gemm(g); return true; }
+  if (!P.oz_gemm(g, h->pack, h->pack_bytes, h->tc_err)) {
+    h->plan_error = true;
+    return false;
+  }
+  return true;
 }
-void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) { P.lu_solve(ds, LU_NB, h->mixed()); }
+void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
+  if (!P.lu_solve(ds, LU_NB, h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64, h->pack, h->pack_bytes, h->tc_err))
+    h->plan_error = true;
+}
 
 // ---------------------------------------------------------- self-energies
 // Builds setup / iteration / final plans for the doubling of 2P lead problems.
@@ -635,7 +645,9 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     // 1. self-energies
     std::vector<int> h_it(2 * P, 0), h_conv(2 * P, 1), h_dinfo(4 * P, 0);
     if (!reuse_sigma) {
+      h->plan_error = false;
       build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd);
+      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the doubling");
       CK(h->p_setup.upload(st), "upload setup");
       CK(h->p_iter[0].upload(st), "upload iter");
       CK(h->p_iter[1].upload(st), "upload iter");
@@ -699,8 +711,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     std::vector<int> h_sinfo, h_binfo(P, 0);
     std::vector<z64> h_tr(P);
     if (want.solve) {
+      h->plan_error = false;
       build_sweeps(h, pts, sinfo, nmax);
       build_boundary(h, pts, want.x ? want.ninj : 0, binfo, h->dtr);
+      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the sweeps");
       CK(h->p_sweep.upload(st), "upload sweeps");
       CK(h->p_bound.upload(st), "upload boundary");
       CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
@@ -822,8 +836,11 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     g_create_error = "non-positive workspace sizes";
     return SS_ERR_ARG;
   }
-  if (cfg->precision != SS_FP64 && cfg->precision != SS_MIXED_BF16X3 && cfg->precision != SS_MIXED_BF16X6) {
-    g_create_error = "unknown precision mode";
+  if (cfg->precision != SS_FP64 && cfg->precision != SS_MIXED_OZAKI) {
+    // The 3/6-product split modes (about 5e-6 relative) are available through
+    // ss_zgemm only: the lead doubling at eta = 1e-10 amplifies their error to
+    // O(1) in band, so the pipeline takes FP64-accurate products.
+    g_create_error = "pipeline precision must be SS_FP64 or SS_MIXED_OZAKI";
     return SS_ERR_ARG;
   }
   if (!(cfg->eta >= 0.0) || !(cfg->decim_tol >= 0.0) || cfg->decim_max_iter < 1) {
@@ -856,11 +873,16 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
   }
   if (h->mixed()) {
     // the largest tensor-core group: the doubling products, 4 GEMMs per lead
-    // with 2 distinct A and 2 distinct B operands of s x s (B packed as 2s rows)
-    const size_t s = cfg->s_b_max;
-    const size_t kp = (size_t)tc_kp((int)s, cfg->precision);
-    const size_t per_lead = 2 * (((s * kp * 2) + 1023) & ~size_t(1023)) + 2 * (((2 * s * kp * 2) + 1023) & ~size_t(1023));
-    h->pack_bytes = (size_t)cfg->max_points * 2 * per_lead + (1 << 20);
+    // with 2 distinct A (s rows) and 2 distinct B (2s rows) operands, each
+    // sliced into S slices of width w
+    const int s = cfg->s_b_max;
+    OzShape sh;
+    oz_plan(s, &sh);
+    const size_t a1 = (((size_t)s * sh.S * sh.w * 2) + 1023) & ~size_t(1023);
+    const size_t b1 = (((size_t)2 * s * sh.S * sh.w * 2) + 1023) & ~size_t(1023);
+    const size_t ex = (((size_t)s * sizeof(int)) + 1023) & ~size_t(1023);
+    const size_t per_lead = 2 * (a1 + ex) + 2 * (b1 + ex);
+    h->pack_bytes = (size_t)cfg->max_points * 2 * per_lead + (4 << 20);
     e = cudaMalloc(&h->pack, h->pack_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->tc_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->tc_err, 0, sizeof(int));
@@ -1034,7 +1056,8 @@ long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
 int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
              int transB, ss_c64* C, int ldc, void* stream) {
   if (m < 0 || n < 0 || k < 1 || !A || !B || !C || lda < 1 || ldb < 1 || ldc < n ||
-      (precision != SS_FP64 && precision != SS_MIXED_BF16X3 && precision != SS_MIXED_BF16X6)) {
+      (precision != SS_FP64 && precision != SS_MIXED_BF16X3 && precision != SS_MIXED_BF16X6 &&
+       precision != SS_MIXED_OZAKI)) {
     g_create_error = "ss_zgemm: bad arguments";
     return SS_ERR_ARG;
   }
@@ -1050,6 +1073,13 @@ int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int t
   cudaError_t e = cudaSuccess;
   if (precision == SS_FP64) {
     plan.gemm(ds);
+  } else if (precision == SS_MIXED_OZAKI) {
+    const size_t cap = Plan::oz_pack_bytes(ds);
+    e = cudaMallocAsync(&pack, cap, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) { cudaGetLastError(); g_create_error = "ss_zgemm: scratch"; return SS_ERR_OOM; }
+    if (!plan.oz_gemm(ds, pack, cap, err)) e = cudaErrorInvalidValue;
   } else {
     const size_t cap = Plan::tc_pack_bytes(ds, precision);
     e = cudaMallocAsync(&pack, cap, st);
@@ -1102,11 +1132,19 @@ int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c
 
 int ss_profile_read(ss_handle* h, int kind, double* total_ms, double* flops, long long* launches) {
   if (!h) return SS_ERR_ARG;
-  if (kind < 0 || kind > K_MEMSET) return fail(h, SS_ERR_ARG, "unknown kernel kind");
+  if (kind < 0 || kind >= K_MEMSET) return fail(h, SS_ERR_ARG, "unknown kernel kind");
   h->prof.collect();
   if (total_ms) *total_ms = h->prof.ms[kind];
   if (flops) *flops = h->prof.flops[kind];
   if (launches) *launches = h->prof.launches[kind];
+  return SS_OK;
+}
+
+int ss_profile_read_issued(ss_handle* h, int kind, double* issued_flops) {
+  if (!h) return SS_ERR_ARG;
+  if (kind < 0 || kind >= K_MEMSET) return fail(h, SS_ERR_ARG, "unknown kernel kind");
+  h->prof.collect();
+  if (issued_flops) *issued_flops = h->prof.issued[kind];
   return SS_OK;
 }
 

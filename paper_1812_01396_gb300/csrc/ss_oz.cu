@@ -1,0 +1,401 @@
+// FP64-accurate complex GEMM on the tcgen05 tensor cores: digit-sliced
+// BF16 operands with exact FP32 accumulation (the Ozaki splitting).
+//
+// Low-precision products are not usable inside the lead doubling: at
+// eta = 1e-10 it amplifies arithmetic error by ~1e6 in band.  So the
+// mixed path keeps FP64 accuracy and still runs its products on the tensor
+// cores:
+//
+//   * every row i of op(A) (real-equivalent [Ar | Ai]) gets a power-of-two
+//     scale 2^eA[i] >= its largest |entry|, every column j of op(B) a scale
+//     2^eB[j] (shared by the re and im rows 2j, 2j+1 of B');
+//   * each scaled value r in (-1, 1) is cut into S integer digits of beta bits,
+//     r = sum_t d_t 2^{-beta (t+1)}, |d_t| <= 2^beta: every digit is an exact
+//     BF16 number;
+//   * A' = [A_0 | A_1 | ... | A_{S-1}] and B' likewise (each slice w >= 2k
+//     wide, zero padded), so the product of digit slices t and u is a plain
+//     K-major BF16 GEMM;
+//   * slices with the same level d = t + u share the scale 2^{-beta (d+2)};
+//     up to np pairs of one level are accumulated in one FP32 TMEM
+//     accumulator, with np * w * 2^{2 beta} < 2^24 so that every partial sum
+//     is an integer below 2^24 and the FP32 accumulation is EXACT;
+//   * each such accumulation ("pass") is drained by the epilogue into FP64
+//     registers, scaled by 2^{eA[i] + eB[j] - beta (d+2)}; four TMEM
+//     accumulators form a ring so the MMA thread runs ahead of the epilogue.
+//
+// Levels d <= S - 1 are kept (the dropped ones are below 2^-54 of the
+// largest product), so the result matches an FP64 GEMM to rounding.
+// One CTA per 128 x 64 tile of C' = A' B'^T; warp 0 issues TMA, warp 1 the
+// MMAs, warps 2-5 drain the accumulators.  Every wait is bounded (2 s).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ss_internal.cuh"
+#include "ss_tc.h"
+#include "ss_tcutil.cuh"
+
+namespace ss {
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 6, NACC = 4;
+constexpr int OZ_THREADS = 192;
+constexpr uint32_t A_BYTES = BM * BK * 2;
+constexpr uint32_t B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 256;  // NACC accumulators of BN columns
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ double pow2(int e) {
+  // 2^e: built from the exponent bits in the normal range, ldexp outside it
+  if (e > -1020 && e < 1020) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __restrict__ descs,
+                                                                const int* __restrict__ tile_start, int nprob,
+                                                                int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[NACC];
+  __shared__ __align__(8) uint64_t acce_bar[NACC];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  __shared__ double colscale[BN / 2];
+
+  const int pid = find_problem(tile_start, nprob, blockIdx.x);
+  const OzDesc& d = descs[pid];
+  if (d.active && __ldg(d.active) == 0) return;
+  const CUtensorMap* map_a = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.ta_off);
+  const CUtensorMap* map_b = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.tb_off);
+  const int tiles_n = (d.n2 + BN - 1) / BN;
+  const int t = blockIdx.x - __ldg(tile_start + pid);
+  const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+  const int wt = d.w / BK;  // K-tiles per slice
+  const int npass = d.npass;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
+    for (int i = 0; i < NACC; ++i) { mbar_init(&accf_bar[i], 1); mbar_init(&acce_bar[i], 128); }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < BN / 2) {
+    const int j = (n0 >> 1) + threadIdx.x;
+    colscale[threadIdx.x] = (2 * j < d.n2) ? pow2(d.eB[j]) : 0.0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: K-tiles of every pass, in order
+    int kt = 0;
+    bool ok = true;
+    for (int p = 0; p < npass && ok; ++p) {
+      const int lev = d.pd[p], t0 = d.pt0[p], np = d.pnp[p];
+      for (int q = 0; q < np && ok; ++q) {
+        const int ta = t0 + q, tb = lev - ta;
+        for (int kk = 0; kk < wt; ++kk, ++kt) {
+          const int st = kt % STAGES;
+          const uint32_t ph = (kt / STAGES) & 1;
+          if (!mbar_wait(&empty_bar[st], ph ^ 1)) { s_fail = 1; ok = false; break; }
+          unsigned char* sa = smem + st * STAGE_BYTES;
+          unsigned char* sb = sa + A_BYTES;
+          mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+          tma_load_2d(sa, map_a, &full_bar[st], ta * d.w + kk * BK, m0);
+          tma_load_2d(sb, map_b, &full_bar[st], tb * d.w + kk * BK, n0);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: one accumulator of the ring per pass
+    int kt = 0;
+    bool ok = true;
+    for (int p = 0; p < npass; ++p) {
+      const int acc = p % NACC, use = p / NACC;
+      if (ok && !mbar_wait(&acce_bar[acc], (use & 1) ^ 1)) { ok = false; s_fail = 1; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int nk = d.pnp[p] * wt;
+      for (int i = 0; i < nk && ok; ++i, ++kt) {
+        const int st = kt % STAGES;
+        const uint32_t ph = (kt / STAGES) & 1;
+        if (!mbar_wait(&full_bar[st], ph)) { ok = false; s_fail = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* sa = smem + st * STAGE_BYTES;
+        unsigned char* sb = sa + A_BYTES;
+        const uint64_t da = smem_desc(sa), db = smem_desc(sb);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          mma_bf16(tmem + acc * BN, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, (i | k) != 0);
+        mma_commit(&empty_bar[st]);
+      }
+      if (ok) mma_commit(&accf_bar[acc]);
+      else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accf_bar[acc])) : "memory");
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: drain every pass into FP64 registers
+    // Every pass sum is an exact integer below 2^24.  They are added in
+    // int64 fixed point with FIX = 37 fractional bits of the level-0 unit
+    // (|total| < 2^24 * 1.1 * 2^37 < 2^62): levels with beta*d <= 37 are
+    // exact, deeper ones round by at most half a unit of 2^-37, so FP64
+    // arithmetic is needed only once per output element.
+    const int q4 = warp & 3;
+    const int row = m0 + q4 * 32 + lane;
+    long long re[BN / 2], im[BN / 2];
+#pragma unroll
+    for (int e = 0; e < BN / 2; ++e) { re[e] = 0; im[e] = 0; }
+    bool ok = true;
+    for (int p = 0; p < npass; ++p) {
+      const int acc = p % NACC, use = p / NACC;
+      if (ok && !mbar_wait(&accf_bar[acc], use & 1)) ok = false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int sh = 37 - d.beta_bits * d.pd[p];  // shift of this level into the fixed point
+      if (ok && !s_fail) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + half * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (sh >= 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              re[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
+              im[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
+            }
+          } else {
+            const int rs = -sh;
+            const long long rnd = 1ll << (rs - 1);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              re[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
+              im[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[acc])) : "memory");
+    }
+    if (ok && !s_fail && row < d.m) {
+      // value = fixed / 2^37 * 2^{-2 beta} * 2^{eA[row]} * 2^{eB[j]}
+      const double rs_row = pow2(d.eA[row] - 37 - 2 * d.beta_bits);
+      const bool unit_alpha = d.alpha.y == 0.0 && (d.alpha.x == 1.0 || d.alpha.x == -1.0);
+#pragma unroll
+      for (int e = 0; e < BN / 2; ++e) {
+        const int j = (n0 >> 1) + e;
+        if (2 * j < d.n2) {
+          const double sc = rs_row * colscale[e];
+          z64 out = zmk((double)re[e] * sc, (double)im[e] * sc);
+          if (unit_alpha) { if (d.alpha.x < 0.0) { out.x = -out.x; out.y = -out.y; } }
+          else out = zmul(d.alpha, out);
+          if (d.cmode == 1) {
+            const size_t fi = (size_t)row * d.ldcf + j;
+            out = zadd(out, zmul(d.beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
+          } else if (d.cmode == 2) {
+            if (row == j) out = zadd(out, d.beta);
+          } else if (d.beta.x != 0.0 || d.beta.y != 0.0) {
+            out = zadd(out, zmul(d.beta, d.c[(size_t)row * d.ldc + j]));
+          }
+          d.c[(size_t)row * d.ldc + j] = out;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0 && err) atomicExch(err, 1);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// --------------------------------------------------------------- scaling
+__device__ __forceinline__ z64 oz_load(const OzPackDesc& p, int i, int j) {
+  const size_t idx = p.trans ? (size_t)j * p.ld + i : (size_t)i * p.ld + j;
+  z64 v = p.x[idx];
+  if (p.s) v = zsub(zmul(p.e, p.s[idx]), v);
+  return p.trans ? zconj(v) : v;
+}
+
+// Exponent e with max |entry| < 2^e over one row of op(A) (role 0) or one
+// column of op(B) (role 1); 0 for an all-zero vector.  One warp per vector;
+// the maximum is taken on the IEEE bits of |x| (monotone for non-negative).
+__global__ void oz_scale_kernel(const OzPackDesc* __restrict__ descs, const int* __restrict__ tile_start,
+                                int nprob) {
+  const int pid = find_problem(tile_start, nprob, blockIdx.x);
+  const OzPackDesc& p = descs[pid];
+  if (p.active && __ldg(p.active) == 0) return;
+  const int v = (blockIdx.x - __ldg(tile_start + pid)) * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int nvec = p.role == 0 ? p.rows : p.rows / 2;
+  if (v >= nvec) return;
+  unsigned long long mx = 0;
+  for (int kk = lane; kk < p.k; kk += 32) {
+    const z64 z = p.role == 0 ? oz_load(p, v, kk) : oz_load(p, kk, v);
+    const unsigned long long a = (unsigned long long)__double_as_longlong(z.x) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(z.y) & 0x7FFFFFFFFFFFFFFFull;
+    mx = a > mx ? a : mx;
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = q > mx ? q : mx;
+  }
+  if (lane == 0) {
+    const int ex = (int)(mx >> 52);
+    // normal: |x| = f 2^(ex-1022), f in [0.5, 1); subnormal rows use the smallest normal scale
+    p.exps[v] = mx == 0 ? 0 : (ex == 0 ? -1021 : ex - 1022);
+  }
+}
+
+// Digits of x / 2^e (|x| < 2^e) for every slice, written at columns t*w + off,
+// using integer arithmetic only: the IEEE mantissa is placed in a signed
+// 62-bit fixed point R = x 2^{62-e}, then digit t is the round-to-nearest
+// quotient of R by 2^{62 - beta (t+1)} and is removed from R.
+__device__ __forceinline__ void write_digits(__nv_bfloat16* row, int w, int off, int S, int beta, double x, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long R = 0;
+  if (ex != 0) {  // zero and subnormals (far below any row scale here) give zero digits
+    const long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int shift = ex - 1013 - e;  // x 2^{62-e} = m 2^{ex-1075+62-e}
+    if (shift >= 0) R = m << shift;   // shift <= 9 because |x| < 2^e
+    else if (shift > -64) R = (m + (1ll << (-shift - 1))) >> (-shift);
+    if (bits >> 63) R = -R;
+  }
+  for (int t = 0; t < S; ++t) {
+    const int sh = 62 - beta * (t + 1);
+    const long long q = (R + (1ll << (sh - 1))) >> sh;
+    R -= q << sh;
+    row[(size_t)t * w + off] = __float2bfloat16_rn((float)q);
+  }
+}
+
+__global__ void oz_pack_kernel(const OzPackDesc* __restrict__ descs, const int* __restrict__ tile_start,
+                               int nprob) {
+  const int pid = find_problem(tile_start, nprob, blockIdx.x);
+  const OzPackDesc& p = descs[pid];
+  if (p.active && __ldg(p.active) == 0) return;
+  const int wtiles = (p.w + 255) / 256;
+  const int tt = blockIdx.x - __ldg(tile_start + pid);
+  const int r = tt / wtiles;
+  const int off = (tt % wtiles) * 256 + threadIdx.x;
+  if (r >= p.rows || off >= p.w) return;
+  __nv_bfloat16* row = p.out + (size_t)r * p.S * p.w;
+  const int k = p.k;
+  if (off >= 2 * k) {
+    for (int t = 0; t < p.S; ++t) row[(size_t)t * p.w + off] = __double2bfloat16(0.0);
+    return;
+  }
+  const int kk = off < k ? off : off - k;
+  double x;
+  int e;
+  if (p.role == 0) {  // A' row r = [Ar | Ai]
+    const z64 v = oz_load(p, r, kk);
+    x = off < k ? v.x : v.y;
+    e = p.exps[r];
+  } else {  // B' rows 2j = [Br | -Bi], 2j+1 = [Bi | Br]
+    const int j = r >> 1;
+    const z64 v = oz_load(p, kk, j);
+    if ((r & 1) == 0) x = off < k ? v.x : -v.y;
+    else x = off < k ? v.y : v.x;
+    e = p.exps[j];
+  }
+  write_digits(row, p.w, off, p.S, p.beta_bits, x, e);
+}
+
+}  // namespace
+
+size_t oz_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+int oz_tiles(int m, int n2) { return ((m + BM - 1) / BM) * ((n2 + BN - 1) / BN); }
+int oz_box_rows_a() { return BM; }
+int oz_box_rows_b() { return BN; }
+
+// Choose beta (bits per digit) for slices of width w: S = ceil(54 / beta)
+// slices; at most npmax digit pairs of one level share an exact FP32 pass
+// (npmax * w * 2^{2 beta} < 2^24).  Cost = tensor K-tiles (pairs * w / 64)
+// plus about four K-tiles per pass drained by the epilogue; the cheapest
+// beta with at most OZ_MAXPASS passes wins.
+void oz_plan(int k, OzShape* sh) {
+  const int w = ((2 * k + BK - 1) / BK) * BK;
+  int best_beta = -1, best_S = 0, best_np = 0;
+  double best_cost = 0.0;
+  for (int beta = 7; beta >= 3; --beta) {
+    const double lim = 16777216.0 / ((double)(1 << (2 * beta)) * (double)w);
+    if (lim <= 1.0) continue;  // not even one pair fits an exact pass
+    const int npmax = (int)((16777215.0 / (double)(1 << (2 * beta))) / (double)w);
+    if (npmax < 1) continue;
+    const int S = (54 + beta - 1) / beta;
+    int npass = 0;
+    for (int lev = 0; lev < S; ++lev) npass += (lev + 1 + npmax - 1) / npmax;
+    if (npass > OZ_MAXPASS) continue;
+    const double cost = (double)S * (S + 1) / 2 * (w / BK) + 4.0 * npass;
+    if (best_beta < 0 || cost < best_cost) { best_beta = beta; best_S = S; best_np = npmax; best_cost = cost; }
+  }
+  sh->w = w;
+  sh->npass = 0;
+  if (best_beta < 0) {  // no exact split for this width: caller must not use the kernel
+    sh->beta = 0;
+    sh->S = 0;
+    sh->npass = OZ_MAXPASS + 1;
+    return;
+  }
+  sh->beta = best_beta;
+  sh->S = best_S;
+  for (int lev = 0; lev < best_S; ++lev) {
+    for (int t0 = 0; t0 < lev + 1; t0 += best_np) {
+      const int np = (lev + 1 - t0) < best_np ? (lev + 1 - t0) : best_np;
+      sh->pd[sh->npass] = (unsigned char)lev;
+      sh->pt0[sh->npass] = (unsigned char)t0;
+      sh->pnp[sh->npass] = (unsigned char)np;
+      sh->npass++;
+    }
+  }
+}
+
+void launch_oz_scale(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st) {
+  if (nprob <= 0 || total <= 0) return;
+  oz_scale_kernel<<<total, 256, 0, st>>>(d, tile_start, nprob);
+}
+void launch_oz_pack(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st) {
+  if (nprob <= 0 || total <= 0) return;
+  oz_pack_kernel<<<total, 256, 0, st>>>(d, tile_start, nprob);
+}
+cudaError_t launch_oz_gemm(const OzDesc* d, const int* tile_start, int nprob, int total, int* err, cudaStream_t st) {
+  if (nprob <= 0 || total <= 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)oz_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  oz_gemm_kernel<<<total, OZ_THREADS, oz_smem_bytes(), st>>>(d, tile_start, nprob, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ss

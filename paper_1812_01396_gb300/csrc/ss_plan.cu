@@ -18,6 +18,122 @@ struct OpKey {
 size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
 }  // namespace
 
+namespace {
+size_t oz_operand_bytes(int rows, int vecs, int k) {
+  OzShape sh;
+  oz_plan(k, &sh);
+  return al1k((size_t)rows * sh.S * sh.w * 2) + al1k((size_t)vecs * sizeof(int));
+}
+}  // namespace
+
+size_t Plan::oz_pack_bytes(const std::vector<GemmDesc>& ds) {
+  std::map<OpKey, int> seen;
+  size_t tot = 0;
+  for (auto& g : ds) {
+    OpKey ka{g.a.p, g.a.s, g.a.e.x, g.a.e.y, g.a.ld, g.a.trans, g.m, g.k, 0};
+    OpKey kb{g.b.p, g.b.s, g.b.e.x, g.b.e.y, g.b.ld, g.b.trans, 2 * g.n, g.k, 1};
+    if (!seen.count(ka)) { seen[ka] = 1; tot += oz_operand_bytes(g.m, g.m, g.k); }
+    if (!seen.count(kb)) { seen[kb] = 1; tot += oz_operand_bytes(2 * g.n, g.n, g.k); }
+  }
+  return tot;
+}
+
+bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err) {
+  if (ds.empty()) return true;
+  std::map<OpKey, int> index;
+  std::vector<OzPackDesc> pk;
+  std::vector<CUtensorMap> maps;
+  std::vector<int> amap(ds.size()), bmap(ds.size());
+  std::vector<OzShape> shapes(ds.size());
+  size_t used = 0;
+  for (size_t i = 0; i < ds.size(); ++i) {
+    const GemmDesc& g = ds[i];
+    oz_plan(g.k, &shapes[i]);
+    const OzShape& sh = shapes[i];
+    if (sh.npass > OZ_MAXPASS) return false;
+    for (int role = 0; role < 2; ++role) {
+      const Operand& o = role == 0 ? g.a : g.b;
+      const int rows = role == 0 ? g.m : 2 * g.n;
+      const int vecs = role == 0 ? g.m : g.n;
+      OpKey key{o.p, o.s, o.e.x, o.e.y, o.ld, o.trans, rows, g.k, role};
+      auto it = index.find(key);
+      int mi;
+      if (it == index.end()) {
+        const size_t bytes = al1k((size_t)rows * sh.S * sh.w * 2);
+        const size_t ebytes = al1k((size_t)vecs * sizeof(int));
+        if (used + bytes + ebytes > cap) return false;
+        OzPackDesc d{};
+        d.x = o.p; d.s = o.s; d.e = o.e; d.ld = o.ld; d.trans = o.trans; d.role = role;
+        d.rows = rows; d.k = g.k; d.w = sh.w; d.S = sh.S; d.beta_bits = sh.beta;
+        d.out = reinterpret_cast<__nv_bfloat16*>(pack + used);
+        d.exps = reinterpret_cast<int*>(pack + used + bytes);
+        d.active = g.active;
+        CUtensorMap m;
+        if (encode_kmajor_map(&m, pack + used, rows, sh.S * sh.w, role == 0 ? oz_box_rows_a() : oz_box_rows_b()) !=
+            cudaSuccess)
+          return false;
+        used += bytes + ebytes;
+        mi = (int)maps.size();
+        maps.push_back(m);
+        pk.push_back(d);
+        index[key] = mi;
+      } else {
+        mi = it->second;
+      }
+      (role == 0 ? amap : bmap)[i] = mi;
+    }
+  }
+  // exponents, then digit slices
+  {
+    std::vector<int> start(pk.size());
+    int tot = 0;
+    for (size_t i = 0; i < pk.size(); ++i) {
+      start[i] = tot;
+      const int nvec = pk[i].role == 0 ? pk[i].rows : pk[i].rows / 2;
+      tot += (nvec + 7) / 8;  // one warp per vector, 8 warps per block
+    }
+    const size_t off = push_vec(pk);
+    LaunchRec r;
+    r.kind = K_OZSCALE; r.off = off; r.toff = push_vec(start); r.nprob = (int)pk.size(); r.tiles = tot;
+    recs_.push_back(r);
+    std::vector<int> start2(pk.size());
+    int tot2 = 0;
+    for (size_t i = 0; i < pk.size(); ++i) { start2[i] = tot2; tot2 += pk[i].rows * ((pk[i].w + 255) / 256); }
+    LaunchRec r2;
+    r2.kind = K_OZPACK; r2.off = off; r2.toff = push_vec(start2); r2.nprob = (int)pk.size(); r2.tiles = tot2;
+    recs_.push_back(r2);
+  }
+  std::vector<OzDesc> ods(ds.size());
+  std::vector<int> start(ds.size());
+  int tot = 0;
+  for (size_t i = 0; i < ds.size(); ++i) {
+    const GemmDesc& g = ds[i];
+    const OzShape& sh = shapes[i];
+    OzDesc t{};
+    t.m = g.m; t.n2 = 2 * g.n; t.w = sh.w; t.kc = g.k; t.beta_bits = sh.beta; t.npass = sh.npass;
+    for (int p = 0; p < sh.npass; ++p) { t.pd[p] = sh.pd[p]; t.pt0[p] = sh.pt0[p]; t.pnp[p] = sh.pnp[p]; }
+    t.eA = pk[amap[i]].exps;
+    t.eB = pk[bmap[i]].exps;
+    t.c = g.c; t.ldc = g.ldc; t.cmode = g.cmode; t.alpha = g.alpha; t.beta = g.beta;
+    t.cs = g.cs; t.ch = g.ch; t.ce = g.ce; t.ldcf = g.ldcf; t.active = g.active;
+    ods[i] = t;
+    start[i] = tot;
+    tot += oz_tiles(t.m, t.n2);
+  }
+  const size_t doff = push(nullptr, ods.size() * sizeof(OzDesc), 64);
+  const size_t moff = push_vec(maps, 64);
+  for (size_t i = 0; i < ds.size(); ++i) {
+    ods[i].ta_off = (long long)(moff + (size_t)amap[i] * sizeof(CUtensorMap) - doff);
+    ods[i].tb_off = (long long)(moff + (size_t)bmap[i] * sizeof(CUtensorMap) - doff);
+  }
+  std::memcpy(host_.data() + doff, ods.data(), ods.size() * sizeof(OzDesc));
+  LaunchRec r;
+  r.kind = K_OZGEMM; r.off = doff; r.toff = push_vec(start); r.nprob = (int)ds.size(); r.tiles = tot;
+  r.p[0] = err;
+  recs_.push_back(r);
+  return true;
+}
+
 size_t Plan::tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode) {
   std::map<OpKey, int> seen;
   size_t tot = 0;
@@ -118,8 +234,13 @@ bool Plan::tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pac
   return true;
 }
 
-void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates) {
-  if (ds.empty()) return;
+bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err) {
+  if (ds.empty()) return true;
+  bool ok = true;
+  auto update = [&](const std::vector<GemmDesc>& g) {
+    if (upd == UPD_EXACT_TC) ok = ok && oz_gemm(g, pack, cap, err);
+    else gemm(g, upd == UPD_FP32);
+  };
   const size_t off = push_vec(ds);
   const int np = (int)ds.size();
   int smax = 0;
@@ -152,12 +273,12 @@ void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates) {
     rr.kind = K_LU_ROW;
     rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.maxc = maxc;
     recs_.push_back(rr);
-    gemm(g, fp32_updates);
+    update(g);
   }
   // backward substitution on the right-hand sides: panels right to left
   int maxrhs = 0;
   for (auto& d : ds) maxrhs = std::max(maxrhs, d.ncols - d.s);
-  if (maxrhs <= 0) return;
+  if (maxrhs <= 0) return ok;
   const int last = ((smax - 1) / nb) * nb;
   for (int k0 = last; k0 >= 0; k0 -= nb) {
     LaunchRec r;
@@ -178,8 +299,9 @@ void Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates) {
       q.active = d.active;
       g.push_back(q);
     }
-    gemm(g, fp32_updates);
+    update(g);
   }
+  return ok;
 }
 
 void Plan::destroy_graph() {
@@ -220,12 +342,28 @@ static bool prof_active(const int* a, const Prof* prof) {
   return !(idx >= 0 && idx < prof->nact && !prof->act_host[idx]);
 }
 
+static double oz_issued(const LaunchRec& r, const std::vector<unsigned char>& host, const Prof* prof) {
+  const OzDesc* g = reinterpret_cast<const OzDesc*>(host.data() + r.off);
+  double f = 0.0;
+  for (int i = 0; i < r.nprob; ++i) {
+    if (!prof_active(g[i].active, prof)) continue;
+    int pairs = 0;
+    for (int p = 0; p < g[i].npass; ++p) pairs += g[i].pnp[p];
+    f += 2.0 * g[i].m * (double)g[i].n2 * (double)pairs * g[i].w;
+  }
+  return f;
+}
+
 static double gemm_flops(const LaunchRec& r, const std::vector<unsigned char>& host, const Prof* prof) {
   double f = 0.0;
   if (r.kind == K_GEMM || r.kind == K_GEMM32) {
     const GemmDesc* g = reinterpret_cast<const GemmDesc*>(host.data() + r.off);
     for (int i = 0; i < r.nprob; ++i)
       if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)g[i].n * g[i].k;
+  } else if (r.kind == K_OZGEMM) {
+    const OzDesc* g = reinterpret_cast<const OzDesc*>(host.data() + r.off);
+    for (int i = 0; i < r.nprob; ++i)
+      if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)(g[i].n2 / 2) * (double)g[i].kc;
   } else if (r.kind == K_TCGEMM) {
     // algorithmic complex flops (8 m n k), not the split-term tensor flops
     const TcDesc* g = reinterpret_cast<const TcDesc*>(host.data() + r.off);
@@ -241,7 +379,10 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     Prof::Rec pr{};
     if (prof && r.kind != K_MEMSET) {
       pr.kind = r.kind;
-      pr.flops = (r.kind == K_GEMM || r.kind == K_TCGEMM || r.kind == K_GEMM32) ? gemm_flops(r, host_, prof) : 0.0;
+      pr.flops = (r.kind == K_GEMM || r.kind == K_TCGEMM || r.kind == K_GEMM32 || r.kind == K_OZGEMM)
+                     ? gemm_flops(r, host_, prof)
+                     : 0.0;
+      pr.issued = r.kind == K_OZGEMM ? oz_issued(r, host_, prof) : 0.0;
       cudaEventCreate(&pr.a);
       cudaEventCreate(&pr.b);
       cudaEventRecord(pr.a, st);
@@ -250,6 +391,14 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     const int* t = reinterpret_cast<const int*>(dev_ + r.toff);
     switch (r.kind) {
       case K_GEMM: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_OZSCALE: launch_oz_scale((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_OZPACK: launch_oz_pack((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_OZGEMM: {
+        cudaError_t e = launch_oz_gemm((const OzDesc*)d, t, r.nprob, r.tiles, (int*)r.p[0], st);
+        if (e != cudaSuccess) return e;
+        ++n;
+        break;
+      }
       case K_GEMM32: launch_zgemm32((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;

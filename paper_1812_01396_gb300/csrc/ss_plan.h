@@ -15,7 +15,7 @@ namespace ss {
 
 // Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
 enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
-                  K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_MEMSET };
+                  K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_OZSCALE, K_OZPACK, K_OZGEMM, K_MEMSET };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -32,13 +32,14 @@ struct LaunchRec {
 // the algorithmic flops of GEMM launches counted only for problems whose
 // `active` flag (mirrored on the host) is set.
 struct Prof {
-  struct Rec { int kind; cudaEvent_t a, b; double flops; };
+  struct Rec { int kind; cudaEvent_t a, b; double flops, issued; };
   std::vector<Rec> recs;
   const int* act_dev = nullptr;   // device flag array the descriptors point into
   const int* act_host = nullptr;  // host mirror of it at launch time
   int nact = 0;
   double ms[K_MEMSET + 1] = {0};
   double flops[K_MEMSET + 1] = {0};
+  double issued[K_MEMSET + 1] = {0};  // flops the tensor pipe executes (digit pairs, padded K)
   long long launches[K_MEMSET + 1] = {0};
   // Fold finished records into the totals (call after a stream sync).
   void collect() {
@@ -46,6 +47,7 @@ struct Prof {
       float t = 0.f;
       if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.kind] += t;
       flops[r.kind] += r.flops;
+      issued[r.kind] += r.issued;
       launches[r.kind] += 1;
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -54,7 +56,7 @@ struct Prof {
   }
   void reset() {
     collect();
-    for (int i = 0; i <= K_MEMSET; ++i) { ms[i] = 0; flops[i] = 0; launches[i] = 0; }
+    for (int i = 0; i <= K_MEMSET; ++i) { ms[i] = 0; flops[i] = 0; issued[i] = 0; launches[i] = 0; }
   }
 };
 
@@ -112,11 +114,18 @@ class Plan {
   // Returns false if the packed operands do not fit or a tensor map fails.
   bool tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pack, size_t cap, int* err);
   static size_t tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode);
+  // FP64-accurate complex GEMMs on the tensor cores (digit-sliced BF16, exact
+  // FP32 accumulation); operands sliced into `pack` as for tc_gemm.
+  bool oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err);
+  static size_t oz_pack_bytes(const std::vector<GemmDesc>& ds);
   // Blocked LU + solve of every problem in ds (panel width nb <= 32; nb <= 0
   // picks the width from the largest block of the group).
-  // fp32_updates: rank-nb trailing and back-substitution updates in FP32
-  // arithmetic (panels, pivots and triangular blocks stay FP64).
-  void lu_solve(const std::vector<LuDesc>& ds, int nb, bool fp32_updates = false);
+  // Arithmetic of the rank-nb trailing and back-substitution updates
+  // (panels, pivots and triangular blocks always stay FP64).
+  enum Updates { UPD_FP64 = 0, UPD_FP32 = 1, UPD_EXACT_TC = 2 };
+  // UPD_EXACT_TC slices the update operands into `pack` (cap bytes).
+  bool lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
+                size_t cap = 0, int* err = nullptr);
   void norm1(const std::vector<Norm1Desc>& ds) {
     if (ds.empty()) return;
     LaunchRec r;

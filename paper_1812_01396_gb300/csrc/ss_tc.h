@@ -39,6 +39,57 @@ struct TcDesc {
   const int* active;
 };
 
+// ---- FP64-accurate digit-sliced GEMM (ss_oz.cu)
+constexpr int OZ_MAXPASS = 32;
+
+// Slicing of one inner dimension k: slice width w (>= 2k, multiple of 64),
+// beta bits per digit, S slices, and the passes (level d, first slice t0,
+// number of pairs np) whose FP32 sums are exact.
+struct OzShape {
+  int w, beta, S, npass;
+  unsigned char pd[OZ_MAXPASS], pt0[OZ_MAXPASS], pnp[OZ_MAXPASS];
+};
+void oz_plan(int k, OzShape* sh);
+
+// One operand to scale and slice.  role 0: A (rows = m, vectors = rows of
+// op(X)); role 1: B (rows = 2n, vectors = columns of op(X)).
+struct OzPackDesc {
+  const z64* x;
+  const z64* s;
+  z64 e;
+  int ld, trans, role;
+  int rows, k, w, S, beta_bits;
+  int* exps;            // per-vector exponents (m or n entries)
+  __nv_bfloat16* out;   // rows x (S * w) row-major
+  const int* active;
+};
+
+struct OzDesc {
+  long long ta_off, tb_off;  // tensor maps, relative to the start of the OzDesc array
+  int m, n2, w, kc, beta_bits, npass;
+  unsigned char pd[OZ_MAXPASS], pt0[OZ_MAXPASS], pnp[OZ_MAXPASS];
+  const int* eA;
+  const int* eB;
+  z64* c;
+  int ldc;
+  int cmode;
+  z64 alpha, beta;
+  const z64* cs;
+  const z64* ch;
+  z64 ce;
+  int ldcf;
+  const int* active;
+};
+
+size_t oz_smem_bytes();
+int oz_tiles(int m, int n2);
+int oz_box_rows_a();
+int oz_box_rows_b();
+void launch_oz_scale(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st);
+void launch_oz_pack(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st);
+cudaError_t launch_oz_gemm(const OzDesc* d, const int* tile_start, int nprob, int total, int* err,
+                           cudaStream_t st);
+
 int tc_kp(int k, int mode);           // padded packed K for mode 1 (3 products) / 2 (6 products)
 int tc_tiles(int m, int n2);
 int pack_tiles(int rows, int kp);
