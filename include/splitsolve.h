@@ -189,6 +189,66 @@ int ss_caroli_transmission_noalloc(int n_pts, int s_b, const ss_c64* sigma_L, co
                                    const ss_c64* G1n, double* T, void* stream);
 const char* ss_noalloc_last_error(void);
 
+/* Autotune the block LU-solve used by every sweep, doubling step and boundary
+ * solve of blocks of size s_b: times a synthetic batch of n_problems
+ * systems [D | B] (s_b x 2 s_b) for each panel width (8 and 16, or 32 above
+ * s_b = 512) and, in SS_MIXED_OZAKI, each update arithmetic (0: FP64 SIMT,
+ * 2: exact tensor-core products), and keeps the fastest for this handle.
+ * cache_path (optional): a text file of lines "precision s_b n_problems nb
+ * upd ms"; a matching line is reused without timing, a new result is appended.
+ * Outputs (optional, host): chosen nb, upd, and its time in ms. */
+int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb, int* upd, double* ms);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start of the surface Green's function (not in the paper).
+ * A 3-layer MLP maps features of (E, k) to the 2 s^2 real/imaginary entries
+ * of one lead's surface Green's function (scaled by out_scale):
+ *   features (n_in = 19): E, cos k, sin k, sin(m pi E), cos(m pi E), m = 1..8;
+ *   layers n_in -> width -> width -> n_out, SiLU, mean-squared loss, Adam.
+ * FP32 master weights, BF16 copies used by every GEMM, FP32 accumulation.
+ * All network arrays are DEVICE pointers, row-major, unless stated.
+ * ------------------------------------------------------------------------ */
+typedef struct ss_mlp ss_mlp;
+
+/* Allocate a network for batches of up to max_batch rows; weights drawn from
+ * U(-1/sqrt(fan_in), +1/sqrt(fan_in)) with a 64-bit LCG seeded by `seed`,
+ * biases zero.  `stream` (cudaStream_t) orders every later call.
+ * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA. */
+int ss_mlp_create(ss_mlp** net, int n_in, int width, int n_out, int max_batch, unsigned long long seed,
+                  void* stream);
+int ss_mlp_destroy(ss_mlp* net);
+/* Replace the FP32 parameters W1 (width x n_in), b1, W2 (width x width), b2,
+ * W3 (n_out x width), b3; params[6] are host (device_ptrs = 0) or device. */
+int ss_mlp_set_params(ss_mlp* net, const float* const* params, int device_ptrs);
+/* Copy the parameters (which = 0) or the last gradients (which = 1) to six
+ * HOST arrays in the order above. */
+int ss_mlp_get(ss_mlp* net, int which, float* const* out);
+/* y (B x n_out, fp32) = network(x), x (B x n_in, fp32); y may be NULL (the
+ * output stays in the network's buffer). */
+int ss_mlp_forward(ss_mlp* net, int B, const float* x, float* y);
+/* Forward, mean-squared loss against t (B x n_out), backward; with lr > 0
+ * also one Adam step (beta1 0.9, beta2 0.999, eps 1e-8).  *loss (host, may
+ * be NULL) receives the loss of this batch (the call then synchronises). */
+int ss_mlp_train_step(ss_mlp* net, int B, const float* x, const float* t, float lr, double* loss);
+const char* ss_mlp_last_error(const ss_mlp* net);
+
+/* Attach a trained network as the warm start of lead `side` (0 left, 1 right)
+ * for k-points with block size s_b = sqrt(n_out / 2); the network is not
+ * owned.  out_scale: the factor the training targets were multiplied by. */
+int ss_set_warm_start(ss_handle* h, ss_mlp* net, int side, double out_scale);
+
+/* Surface Green's function g of lead `side` at E[p] + i*eta for the Hamiltonian
+ * k_id[p] (s_b*s_b complex per point, packed; device or host per
+ * cfg.device_ptrs).  kval[p] (host) is the transverse momentum fed to the
+ * network.  With a warm start attached and use_warm = 1: g0 from the network,
+ * then at most warm_iters steps of g <- (D - U g L)^-1 (right lead;
+ * (D - L g U)^-1 left), accepted when ||g (D - U g L) - 1||_F / sqrt(s_b) <=
+ * warm_tol; otherwise the plain doubling result is returned.  iters (host,
+ * optional): fixed-point steps or doubling steps per point; seeded (host,
+ * optional): 1 where the warm start was accepted. */
+int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, const double* kval, int side,
+                  int use_warm, int warm_iters, double warm_tol, ss_c64* g, int* iters, int* seeded, int* status);
+
 /* Kernel kinds for ss_profile_read. */
 #define SS_KERNEL_ZGEMM      0  /* batched complex GEMM (all GEMM-shaped steps)      */
 #define SS_KERNEL_FORM       1  /* elementwise forms / copies                         */
@@ -206,6 +266,9 @@ const char* ss_noalloc_last_error(void);
 #define SS_KERNEL_OZ_SCALE  13  /* row/column power-of-two scales of the exact GEMM   */
 #define SS_KERNEL_OZ_PACK   14  /* BF16 digit slices of the exact GEMM                */
 #define SS_KERNEL_OZGEMM    15  /* digit-sliced tcgen05 GEMM, exact FP32 accumulation */
+#define SS_KERNEL_FROB2     16  /* Frobenius norms (warm-start judge, refinement)     */
+#define SS_KERNEL_ZGEMM_LU  17  /* SS_KERNEL_ZGEMM launches issued by the block LU    */
+#define SS_KERNEL_OZGEMM_LU 18  /* SS_KERNEL_OZGEMM launches issued by the block LU   */
 
 /* With cfg.profile = 1: total device time (ms, CUDA events around each
  * launch on cfg.stream), algorithmic flops (GEMM kind only: 8 m n k per

@@ -29,10 +29,12 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGU
 EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve",
            "ss_transmission", "ss_destroy", "ss_last_error", "ss_launch_count", "ss_profile_read",
            "ss_profile_reset", "ss_profile_read_issued", "ss_zgemm", "ss_caroli_transmission",
-           "ss_caroli_transmission_noalloc", "ss_noalloc_last_error")
+           "ss_caroli_transmission_noalloc", "ss_noalloc_last_error", "ss_mlp_create", "ss_mlp_destroy",
+           "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward", "ss_mlp_train_step", "ss_mlp_last_error",
+           "ss_set_warm_start", "ss_surface_gf", "ss_autotune")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
                 "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
-                "oz_scale": 13, "oz_pack": 14, "ozgemm": 15}
+                "oz_scale": 13, "oz_pack": 14, "ozgemm": 15, "frob2": 16, "zgemm_lu": 17, "ozgemm_lu": 18}
 
 
 class SSConfig(C.Structure):
@@ -90,6 +92,22 @@ def load_library(path: str = LIB_PATH):
     lib.ss_caroli_transmission_noalloc.restype = C.c_int
     lib.ss_noalloc_last_error.argtypes = []
     lib.ss_noalloc_last_error.restype = C.c_char_p
+    fp = C.POINTER(C.c_float)
+    lib.ss_mlp_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, vp]
+    lib.ss_mlp_destroy.argtypes = [vp]
+    lib.ss_mlp_set_params.argtypes = [vp, C.POINTER(vp), C.c_int]
+    lib.ss_mlp_get.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    lib.ss_mlp_forward.argtypes = [vp, C.c_int, vp, vp]
+    lib.ss_mlp_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
+    lib.ss_mlp_last_error.argtypes = [vp]
+    lib.ss_mlp_last_error.restype = C.c_char_p
+    lib.ss_set_warm_start.argtypes = [vp, vp, C.c_int, C.c_double]
+    lib.ss_autotune.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, ip, ip, dp]
+    lib.ss_autotune.restype = C.c_int
+    lib.ss_surface_gf.argtypes = [vp, C.c_int, dp, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double, vp, ip, ip, ip]
+    for name in ("ss_mlp_create", "ss_mlp_destroy", "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward",
+                 "ss_mlp_train_step", "ss_set_warm_start", "ss_surface_gf"):
+        getattr(lib, name).restype = C.c_int
     for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
                  "ss_destroy"):
         getattr(lib, name).restype = C.c_int
@@ -279,6 +297,40 @@ class Handle:
                 o += n * s * n_inj
         return out, st, rc
 
+    def autotune(self, s_b, n_problems, cache_path=None):
+        """ss_autotune: returns (panel width, update arithmetic, ms)."""
+        nb, upd, ms = C.c_int(), C.c_int(), C.c_double()
+        cp = None if cache_path is None else str(cache_path).encode()
+        self._check(self._lib.ss_autotune(self._h, int(s_b), int(n_problems), cp, C.byref(nb), C.byref(upd),
+                                          C.byref(ms)))
+        return nb.value, upd.value, ms.value
+
+    def set_warm_start(self, net, side, out_scale):
+        """ss_set_warm_start: attach a trained MLP to lead `side` (0 left, 1 right)."""
+        self._check(self._lib.ss_set_warm_start(self._h, net._n, int(side), float(out_scale)))
+        self._warm = net  # keep it alive while attached
+
+    def surface_gf(self, E, k_id, kval=None, side=1, use_warm=False, warm_iters=8, warm_tol=1e-10,
+                   allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
+        """ss_surface_gf; returns (g list of (s,s), iters, seeded, status, rc)."""
+        E, k = self._pts(E, k_id)
+        P = E.size
+        kv = None if kval is None else np.ascontiguousarray(np.broadcast_to(np.atleast_1d(kval), E.shape),
+                                                            dtype=np.float64)
+        tot = int(sum(self.shapes[int(q)][1] ** 2 for q in k))
+        g = self._alloc(tot, np.complex128)
+        it = np.zeros(P, np.int32)
+        sd = np.zeros(P, np.int32)
+        st = np.zeros(P, np.int32)
+        rc = self._lib.ss_surface_gf(self._h, P, E.ctypes.data_as(C.POINTER(C.c_double)),
+                                     k.ctypes.data_as(C.POINTER(C.c_int)),
+                                     None if kv is None else kv.ctypes.data_as(C.POINTER(C.c_double)), int(side),
+                                     int(bool(use_warm)), int(warm_iters), float(warm_tol), _ptr(g),
+                                     it.ctypes.data_as(C.POINTER(C.c_int)), sd.ctypes.data_as(C.POINTER(C.c_int)),
+                                     st.ctypes.data_as(C.POINTER(C.c_int)))
+        self._check(rc, allow)
+        return self._split(g, k), it, sd, st, rc
+
     def transmission(self, E, k_id, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
         """Returns (T (P,), err_est (P,), status (P,), rc)."""
         E, k = self._pts(E, k_id)
@@ -334,3 +386,65 @@ def ss_caroli_transmission_noalloc(sigma_L, sigma_R, G1n, T, stream=None):
     rc = lib.ss_caroli_transmission_noalloc(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
     if rc != SS_OK:
         raise SSError(rc, lib.ss_noalloc_last_error().decode())
+
+
+class MLP:
+    """Warm-start network run by the library's kernels (ss_mlp_*).
+
+    Arrays passed to forward/train_step are torch CUDA float32 tensors."""
+
+    def __init__(self, n_in, width, n_out, max_batch, seed=0, stream=None):
+        lib = load_library()
+        n = C.c_void_p()
+        rc = lib.ss_mlp_create(C.byref(n), int(n_in), int(width), int(n_out), int(max_batch), int(seed), stream)
+        if rc != SS_OK:
+            raise SSError(rc, "ss_mlp_create failed")
+        self._n, self._lib = n, lib
+        self.n_in, self.width, self.n_out, self.max_batch = n_in, width, n_out, max_batch
+        self.shapes = [(width, n_in), (width,), (width, width), (width,), (n_out, width), (n_out,)]
+
+    def close(self):
+        if getattr(self, "_n", None):
+            self._lib.ss_mlp_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != SS_OK:
+            raise SSError(rc, self._lib.ss_mlp_last_error(self._n).decode())
+
+    def set_params(self, params):
+        arrs = [np.ascontiguousarray(p, dtype=np.float32) for p in params]
+        ptrs = (C.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+        self._check(self._lib.ss_mlp_set_params(self._n, ptrs, 0))
+
+    def _get(self, which):
+        out = [np.zeros(sh, np.float32) for sh in self.shapes]
+        ptrs = (C.c_void_p * 6)(*[a.ctypes.data for a in out])
+        self._check(self._lib.ss_mlp_get(self._n, which, ptrs))
+        return out
+
+    def get_params(self):
+        return self._get(0)
+
+    def get_grads(self):
+        return self._get(1)
+
+    def forward(self, x):
+        import torch
+        x = _dev_in(x)
+        y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        self._check(self._lib.ss_mlp_forward(self._n, int(x.shape[0]), _ptr(x), _ptr(y)))
+        return y
+
+    def train_step(self, x, t, lr):
+        x, t = _dev_in(x), _dev_in(t)
+        loss = C.c_double()
+        self._check(self._lib.ss_mlp_train_step(self._n, int(x.shape[0]), _ptr(x), _ptr(t), float(lr),
+                                                C.byref(loss)))
+        return loss.value

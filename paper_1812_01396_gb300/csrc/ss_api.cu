@@ -16,6 +16,9 @@
 
 #include <algorithm>
 #include <cmath>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -79,27 +82,14 @@ struct PW {
   int* ipr;
   z64* inj;  // device copy or user pointer (2s x ninj)
   z64* x;    // device output (N x ninj)
+  // FP64 iterative refinement of x (mixed mode): D_i^-1 of the first-column
+  // sweep, R^-1, residual r, UL-substitution work w, SMW work zc, t
+  z64 *Dinv = nullptr, *r = nullptr, *wv = nullptr, *zc = nullptr, *tv = nullptr;
 };
 
-size_t point_bytes(int n, int s, int ninj) {
-  Carve c(nullptr);
-  const size_t ss2 = (size_t)s * s;
-  for (int q = 0; q < 2; ++q) {
-    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
-    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
-    c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(3 * ss2); c.take<int>(s);
-    c.take<z64>(ss2);
-    c.take<z64>((size_t)n * ss2); c.take<z64>(2 * ss2); c.take<z64>(ss2); c.take<int>(s);
-  }
-  c.take<z64>((size_t)2 * s * (3 * s + ninj)); c.take<z64>((size_t)2 * s * ninj);
-  c.take<z64>((size_t)2 * s * ninj); c.take<z64>(ss2); c.take<z64>(ss2); c.take<z64>(ss2);
-  c.take<z64>(ss2); c.take<z64>(ss2); c.take<int>(2 * s);
-  c.take<z64>((size_t)2 * s * ninj);          // injection staging
-  c.take<z64>((size_t)n * s * ninj);          // x staging
-  return c.off + 256;
-}
-
-void carve_point(Carve& c, PW& w, int ninj) {
+// Workspace of one point; with `ir` also the refinement buffers.  The layout
+// depends only on (n, s, ninj, ir), so cached results keep their addresses.
+void carve_point(Carve& c, PW& w, int ninj, bool ir = false) {
   const int n = w.n, s = w.s;
   const size_t ss2 = (size_t)s * s;
   for (int q = 0; q < 2; ++q) {
@@ -109,15 +99,31 @@ void carve_point(Carve& c, PW& w, int ninj) {
     w.T1[q] = c.take<z64>(ss2); w.T2[q] = c.take<z64>(ss2); w.Wd[q] = c.take<z64>(3 * ss2);
     w.ipd[q] = c.take<int>(s);
     w.sig[q] = c.take<z64>(ss2);
-    w.X[q] = c.take<z64>((size_t)n * ss2); w.Ws[q] = c.take<z64>(2 * ss2); w.tmp[q] = c.take<z64>(ss2);
+    w.X[q] = c.take<z64>((size_t)n * ss2); w.Ws[q] = c.take<z64>(3 * ss2); w.tmp[q] = c.take<z64>(ss2);
     w.ips[q] = c.take<int>(s);
   }
-  w.Rw = c.take<z64>((size_t)2 * s * (3 * s + ninj)); w.gb = c.take<z64>((size_t)2 * s * ninj);
+  const int ldr = 3 * s + ninj + (ir ? 2 * s : 0);
+  w.Rw = c.take<z64>((size_t)2 * s * ldr); w.gb = c.take<z64>((size_t)2 * s * ninj);
   w.cv = c.take<z64>((size_t)2 * s * ninj); w.G1n = c.take<z64>(ss2);
   w.Gam[0] = c.take<z64>(ss2); w.Gam[1] = c.take<z64>(ss2); w.M1 = c.take<z64>(ss2); w.M2 = c.take<z64>(ss2);
   w.ipr = c.take<int>(2 * s);
   w.inj = c.take<z64>((size_t)2 * s * ninj);
   w.x = c.take<z64>((size_t)n * s * ninj);
+  if (ir) {
+    w.Dinv = c.take<z64>((size_t)n * ss2);
+    w.r = c.take<z64>((size_t)n * s * ninj);
+    w.wv = c.take<z64>((size_t)n * s * ninj);
+    w.zc = c.take<z64>((size_t)2 * s * ninj);
+    w.tv = c.take<z64>((size_t)2 * s * ninj);
+  }
+}
+
+size_t point_bytes(int n, int s, int ninj, bool ir = false) {
+  Carve c(nullptr);
+  PW w;
+  w.n = n; w.s = s;
+  carve_point(c, w, ninj, ir);
+  return c.off + 256;
 }
 
 // ------------------------------------------------------------ descriptors
@@ -191,6 +197,19 @@ struct ss_handle {
   int* tc_err = nullptr;
   bool mixed() const { return cfg.precision != SS_FP64; }
   bool plan_error = false;  // a tensor-core group did not fit the packing buffer
+  // learned warm start
+  ss_mlp* warm_net[2] = {nullptr, nullptr};
+  double warm_scale[2] = {1.0, 1.0};
+  float* feat = nullptr;    // max_points x n_in features
+  float* warm_y = nullptr;  // max_points x n_out network outputs
+  double* wres = nullptr;   // per-point Dyson residual (sum of squares)
+  size_t warm_cap = 0;
+  Plan p_warm_iter, p_warm_judge, p_final_g;
+  Plan p_ir_res, p_ir_cor;
+  // autotuned LU settings per block size: panel width and update arithmetic
+  struct Tune { int nb; int upd; double ms; };
+  std::map<int, Tune> tune;
+  std::vector<double> c_err;  // relative FP64 residual of the last refined solve
   Prof* P() { return cfg.profile ? &prof : nullptr; }
   // cache of the last chunk
   std::vector<double> cE;
@@ -229,14 +248,19 @@ bool big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
   return true;
 }
 void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
-  if (!P.lu_solve(ds, LU_NB, h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64, h->pack, h->pack_bytes, h->tc_err))
-    h->plan_error = true;
+  int smax = 0;
+  for (auto& d : ds) smax = std::max(smax, d.s);
+  int nb = LU_NB;
+  Plan::Updates upd = h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64;
+  auto it = h->tune.find(smax);
+  if (it != h->tune.end()) { nb = it->second.nb; upd = (Plan::Updates)it->second.upd; }
+  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err)) h->plan_error = true;
 }
 
 // ---------------------------------------------------------- self-energies
 // Builds setup / iteration / final plans for the doubling of 2P lead problems.
 void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, int* conv,
-                      int* info, double* na, double* nb, double* nd) {
+                      int* info, double* na, double* nb, double* nd, bool preset_act = false) {
   const int P = (int)pts.size();
   const int NP = 2 * P;
   const double eta = h->cfg.eta;
@@ -262,7 +286,7 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
   S.memset0(na, sizeof(double) * NP);
   S.memset0(nb, sizeof(double) * NP);
   S.memset0(nd, sizeof(double) * NP);
-  S.fill(act, NP, 1);
+  if (!preset_act) S.fill(act, NP, 1);
   S.memset0(iters, sizeof(int) * NP);
   S.memset0(conv, sizeof(int) * NP);
   S.memset0(info, sizeof(int) * NP * 2);
@@ -363,6 +387,7 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
   Plan& S = h->p_sweep;
   S.clear();
   const int P = (int)pts.size();
+  const bool ir = h->mixed();  // first-column sweep also returns D_i^-1 for the refinement
   S.memset0(info, sizeof(int) * 2 * P * nmax);
   for (int t = 0; t < nmax; ++t) {
     std::vector<GemmDesc> g;
@@ -370,13 +395,15 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
     std::vector<LuDesc> lu;
     for (int p = 0; p < P; ++p) {
       PW& w = pts[p];
-      const int n = w.n, s = w.s, ld = 2 * s;
+      const int n = w.n, s = w.s;
       if (t >= n) continue;
       const KData* kd = w.kd;
       const size_t ss2 = (size_t)s * s;
       const z64 E = make_double2(w.E, 0.0);
       for (int dir = 0; dir < 2; ++dir) {
         const int i = dir == 0 ? n - t : t + 1;  // 1-based block
+        const bool with_inv = ir && dir == 0;
+        const int ld = with_inv ? 3 * s : 2 * s;
         z64* W = w.Ws[dir];
         const z64* Sii = kd->Sd + (i - 1) * ss2;
         const z64* Hii = kd->Hd + (i - 1) * ss2;
@@ -399,11 +426,13 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
           if (i < n) f.push_back(fformed(W + s, ld, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s, 0));
           else f.push_back(fident(W + s, ld, s, s, 1.0));
         }
+        if (with_inv) f.push_back(fident(W + 2 * s, ld, s, s, 1.0));
         LuDesc L{};
-        L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ips[dir];
+        L.w = W; L.ldw = ld; L.s = s; L.ncols = with_inv ? 3 * s : 2 * s; L.ipiv = w.ips[dir];
         L.info = info + (size_t)(2 * p + dir) * nmax + t;
         lu.push_back(L);
         fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, W + s, ld, s, s));
+        if (with_inv) fc.push_back(fcopy(w.Dinv + (i - 1) * ss2, s, W + 2 * s, ld, s, s));
       }
     }
     big_gemm(h, S, g);
@@ -443,9 +472,10 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
   std::vector<GemmDesc> gR, gb1, gb2, gsb, gG1, gG2, gx1, gx2, gM;
   std::vector<LuDesc> lu;
   std::vector<TraceDesc> tr;
+  const bool ir = h->mixed() && ninj > 0;
   for (int p = 0; p < P; ++p) {
     PW& w = pts[p];
-    const int n = w.n, s = w.s, ld = 3 * s + ninj;
+    const int n = w.n, s = w.s, ld = 3 * s + ninj + (ir ? 2 * s : 0);
     const size_t ss2 = (size_t)s * s;
     const z64* G11 = w.X[0];
     const z64* Gn1 = w.X[0] + (size_t)(n - 1) * ss2;
@@ -454,6 +484,7 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
     z64* R = w.Rw;
     f0.push_back(fident(R + 2 * s, ld, s, s, 0.0));
     f0.push_back(fident(R + (size_t)s * ld + 2 * s, ld, s, s, 1.0));
+    if (ir) f0.push_back(fident(R + 3 * s + ninj, ld, 2 * s, 2 * s, 1.0));  // R^-1 for the refinement
     GemmDesc q;
     q = gdesc(s, s, s, plain(w.sig[0], s), plain(G11, s), R, ld, MONE, ONE); q.cmode = 2; gR.push_back(q);
     gR.push_back(gdesc(s, s, s, plain(w.sig[0], s), plain(G1n, s), R + s, ld, MONE, ZERO));
@@ -517,6 +548,130 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
   B.trace(tr);
 }
 
+// ------------------------------------------------------------ refinement
+// Residual r = Inj - (A - Sigma) x in FP64 for every block, and ||r||_F^2.
+void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr, double* bb) {
+  Plan& R = h->p_ir_res;
+  R.clear();
+  const int P = (int)pts.size();
+  R.memset0(rr, sizeof(double) * P);
+  std::vector<FormDesc> f;
+  std::vector<GemmDesc> gd, gu, gl, gs1, gs2;
+  std::vector<Norm1Desc> nr;
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const int n = w.n, s = w.s;
+    const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
+    const KData* kd = w.kd;
+    const z64 E = make_double2(w.E, 0.0);
+    for (int i = 1; i <= n; ++i) {
+      z64* ri = w.r + (i - 1) * bs;
+      FormDesc fd = fdesc(ri, ninj, s, ninj);
+      if (i == 1) { fd.x = w.inj; fd.ldx = ninj; fd.ax = ONE; }
+      if (i == n) { fd.y = w.inj + bs; fd.ldy = ninj; fd.ay = ONE; }
+      f.push_back(fd);
+      const z64* xi = w.x + (i - 1) * bs;
+      gd.push_back(gdesc(s, ninj, s, formed(kd->Sd + (i - 1) * ss2, kd->Hd + (i - 1) * ss2, E, s), plain(xi, ninj), ri,
+                         ninj, MONE, ONE));
+      if (i < n)
+        gu.push_back(gdesc(s, ninj, s, formed(kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s), plain(xi + bs, ninj),
+                           ri, ninj, MONE, ONE));
+      if (i > 1)
+        gl.push_back(gdesc(s, ninj, s, formed(kd->Su + (i - 2) * ss2, kd->Hu + (i - 2) * ss2, E, s, 1),
+                           plain(xi - bs, ninj), ri, ninj, MONE, ONE));
+    }
+    gs1.push_back(gdesc(s, ninj, s, plain(w.sig[0], s), plain(w.x, ninj), w.r, ninj, ONE, ONE));
+    gs2.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.x + (n - 1) * bs, ninj), w.r + (n - 1) * bs, ninj, ONE,
+                        ONE));
+    nr.push_back({w.r, ninj, n * s, ninj, rr + p, nullptr});
+  }
+  R.form(f);
+  R.gemm(gd);
+  R.gemm(gu);
+  R.gemm(gl);
+  R.gemm(gs1);
+  R.gemm(gs2);
+  R.frob2(nr);
+  (void)bb;
+}
+
+// Correction delta = M~^-1 r with the stored D_i^-1 (block UL substitution of
+// the first-column sweep) and R^-1 (Sherman-Morrison-Woodbury), then x += delta.
+// The correction only has to be approximate, so its products use FP32 arithmetic.
+void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax) {
+  Plan& C = h->p_ir_cor;
+  C.clear();
+  const int P = (int)pts.size();
+  // backward: w_n = Dn^-1 r_n ; w_i = Di^-1 (r_i - U_i w_{i+1})
+  for (int t = 0; t < nmax; ++t) {
+    std::vector<FormDesc> f;
+    std::vector<GemmDesc> g1, g2;
+    for (auto& w : pts) {
+      const int n = w.n, s = w.s;
+      if (t >= n) continue;
+      const int i = n - t;
+      const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
+      const z64 E = make_double2(w.E, 0.0);
+      z64* ri = w.r + (i - 1) * bs;
+      z64* wi = w.wv + (i - 1) * bs;
+      if (i == n) {
+        g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(ri, ninj), wi, ninj, ONE, ZERO));
+      } else {
+        f.push_back(fcopy(w.tv, ninj, ri, ninj, s, ninj));
+        g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 1) * ss2, w.kd->Hu + (i - 1) * ss2, E, s),
+                           plain(wi + bs, ninj), w.tv, ninj, MONE, ONE));
+        g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, ONE, ZERO));
+      }
+    }
+    C.form(f);
+    C.gemm(g1, true);
+    C.gemm(g2, true);
+  }
+  // forward: y_1 = w_1 ; y_i = w_i - Di^-1 (U_{i-1}^H y_{i-1})  (in place in w)
+  for (int t = 1; t < nmax; ++t) {
+    std::vector<GemmDesc> g1, g2;
+    for (auto& w : pts) {
+      const int n = w.n, s = w.s;
+      if (t >= n) continue;
+      const int i = t + 1;
+      const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
+      const z64 E = make_double2(w.E, 0.0);
+      z64* wi = w.wv + (i - 1) * bs;
+      g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 2) * ss2, w.kd->Hu + (i - 2) * ss2, E, s, 1),
+                         plain(wi - bs, ninj), w.tv, ninj, ONE, ZERO));
+      g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, MONE, ONE));
+    }
+    C.gemm(g1, true);
+    C.gemm(g2, true);
+  }
+  // SMW: z' = R^-1 [Sigma_L y_1 ; Sigma_R y_n] ; x_i += y_i + Q_i z'_top + P_i z'_bot
+  std::vector<GemmDesc> gz1, gz2, gr, gx1, gx2;
+  std::vector<FormDesc> fx;
+  for (auto& w : pts) {
+    const int n = w.n, s = w.s;
+    const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
+    const int ld = 3 * s + ninj + 2 * s;
+    gz1.push_back(gdesc(s, ninj, s, plain(w.sig[0], s), plain(w.wv, ninj), w.zc, ninj, ONE, ZERO));
+    gz2.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.wv + (n - 1) * bs, ninj), w.zc + bs, ninj, ONE, ZERO));
+    gr.push_back(gdesc(2 * s, ninj, 2 * s, plain(w.Rw + 3 * s + ninj, ld), plain(w.zc, ninj), w.tv, ninj, ONE, ZERO));
+    for (int i = 0; i < n; ++i) {
+      z64* xi = w.x + i * bs;
+      FormDesc fd = fcopy(xi, ninj, xi, ninj, s, ninj);
+      fd.y = w.wv + i * bs; fd.ldy = ninj; fd.ay = ONE;
+      fx.push_back(fd);
+      gx1.push_back(gdesc(s, ninj, s, plain(w.X[0] + i * ss2, s), plain(w.tv, ninj), xi, ninj, ONE, ONE));
+      gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.tv + bs, ninj), xi, ninj, ONE, ONE));
+    }
+  }
+  C.gemm(gz1, true);
+  C.gemm(gz2, true);
+  C.gemm(gr, true);
+  C.form(fx);
+  C.gemm(gx1, true);
+  C.gemm(gx2, true);
+  (void)P;
+}
+
 bool same_points(const ss_handle* h, int n, const double* E, const int* k) {
   if ((int)h->cE.size() != n) return false;
   for (int i = 0; i < n; ++i)
@@ -566,6 +721,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
   if (want.ninj < 0 || want.ninj > h->cfg.max_inj) return fail(h, SS_ERR_ARG, "n_inj outside 1..max_inj");
   status.assign(n_pts, SS_OK);
   iters.assign(2 * n_pts, 0);
+  std::vector<double> err_out(n_pts, -1.0);
   T.assign(n_pts, 0.0);
   Ti.assign(n_pts, 0.0);
   // offsets of per-point packed arrays
@@ -602,7 +758,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     while (pos < (size_t)n_pts && (int)pts.size() < h->cfg.max_points) {
       const int i = order[pos];
       const KData& kd = h->ks[k_id[i]];
-      const size_t need = point_bytes(kd.n, kd.s, h->cfg.max_inj);
+      const size_t need = point_bytes(kd.n, kd.s, h->cfg.max_inj, h->mixed());
       if (!pts.empty() && bytes + need > h->arena_bytes) break;
       if (need > h->arena_bytes) return fail(h, SS_ERR_OOM, "one point does not fit the workspace");
       bytes += need;
@@ -616,10 +772,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     // stay at the same addresses whatever n_inj the next call uses
     Carve c(h->arena);
     int nmax = 0;
-    for (auto& w : pts) { carve_point(c, w, h->cfg.max_inj); nmax = std::max(nmax, w.n); }
+    for (auto& w : pts) { carve_point(c, w, h->cfg.max_inj, h->mixed()); nmax = std::max(nmax, w.n); }
     // device scalars: act, iters, conv (2P each), decim info (4P), sweep info (2P*nmax), bound info (P)
     const size_t ni = 2 * P * 3 + 4 * P + 2 * (size_t)P * nmax + P;
-    int rc = ensure_scalars(h, ni, 3 * 2 * P, P);
+    int rc = ensure_scalars(h, ni, 3 * 2 * P + 2 * P, P);
     if (rc) return rc;
     int* act = h->dint;
     int* itr = act + 2 * P;
@@ -630,6 +786,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     double* na = h->ddbl;
     double* nb = na + 2 * P;
     double* nd = nb + 2 * P;
+    double* rr = nd + 2 * P;  // refinement: ||r||^2 and ||Inj||^2 per point
+    double* bb = rr + P;
 
     // inputs
     if (want.solve && want.ninj > 0) {
@@ -710,6 +868,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     // 2.-4. sweeps, boundary, transmission
     std::vector<int> h_sinfo, h_binfo(P, 0);
     std::vector<z64> h_tr(P);
+    std::vector<double> ir_err(P, -1.0);
+    int ir_steps = 0;
     if (want.solve) {
       h->plan_error = false;
       build_sweeps(h, pts, sinfo, nmax);
@@ -719,6 +879,36 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       CK(h->p_bound.upload(st), "upload boundary");
       CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
       CK(h->p_bound.run(st, &h->nlaunch, h->P()), "boundary");
+      if (h->mixed() && want.x && want.ninj > 0) {
+        // FP64 iterative refinement of x until ||r|| <= ir_tol ||Inj|| or the cap
+        build_ir_residual(h, pts, want.ninj, rr, bb);
+        build_ir_correction(h, pts, want.ninj, nmax);
+        Plan nrm;
+        std::vector<Norm1Desc> nb_d;
+        for (int p = 0; p < P; ++p) nb_d.push_back({pts[p].inj, want.ninj, 2 * pts[p].s, want.ninj, bb + p, nullptr});
+        nrm.memset0(bb, sizeof(double) * P);
+        nrm.frob2(nb_d);
+        CK(nrm.upload(st), "upload");
+        CK(nrm.run(st, &h->nlaunch, h->P()), "||Inj||");
+        CK(h->p_ir_res.upload(st), "upload");
+        CK(h->p_ir_cor.upload(st), "upload");
+        std::vector<double> hr(P), hb(P);
+        CK(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
+        for (int it = 0;; ++it) {
+          CK(h->p_ir_res.run(st, &h->nlaunch, h->P()), "residual");
+          CK(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
+          CK(cudaStreamSynchronize(st), "refinement sync");
+          double worst_rel = 0.0;
+          for (int p = 0; p < P; ++p) {
+            const double rel = std::sqrt(hr[p] / std::max(hb[p], 1e-300));
+            ir_err[p] = rel;
+            worst_rel = std::max(worst_rel, std::isfinite(rel) ? rel : 1e300);
+          }
+          ir_steps = it;
+          if (worst_rel <= h->cfg.ir_tol || it >= h->cfg.ir_max_iter) break;
+          CK(h->p_ir_cor.run(st, &h->nlaunch, h->P()), "correction");
+        }
+      }
       h_sinfo.assign(2 * (size_t)P * nmax, 0);
       CK(cudaMemcpyAsync(h_sinfo.data(), sinfo, sizeof(int) * h_sinfo.size(), cudaMemcpyDeviceToHost, st), "info");
       CK(cudaMemcpyAsync(h_binfo.data(), binfo, sizeof(int) * P, cudaMemcpyDeviceToHost, st), "info");
@@ -754,6 +944,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
               break;
             }
         if (h_binfo[p] && stt == SS_OK) stt = SS_ERR_SINGULAR;
+        if (ir_err[p] >= 0.0) {
+          err_out[i] = ir_err[p];
+          if (stt == SS_OK && !(ir_err[p] <= h->cfg.ir_tol)) stt = SS_ERR_NOT_CONVERGED;
+        }
         if (stt == SS_OK && !(std::isfinite(h_tr[p].x) && std::isfinite(h_tr[p].y))) {
           stt = SS_ERR_SINGULAR;
           h->err = "non-finite transmission at point " + std::to_string(i);
@@ -774,6 +968,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
   h->cT = T;
   h->cTi = Ti;
   h->c_status = status;
+  h->c_err = err_out;
   return rc_all;
 }
 
@@ -863,7 +1058,8 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return SS_ERR_CUDA; }
     h->own_stream = true;
   }
-  h->arena_bytes = (size_t)cfg->max_points * point_bytes(cfg->n_b_max, cfg->s_b_max, cfg->max_inj);
+  h->arena_bytes = (size_t)cfg->max_points *
+                   point_bytes(cfg->n_b_max, cfg->s_b_max, cfg->max_inj, cfg->precision == SS_MIXED_OZAKI);
   e = cudaMalloc(&h->arena, h->arena_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1012,7 +1208,10 @@ int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, d
     if (st.empty()) return rc;
   }
   std::vector<double> err(n_pts);
-  for (int i = 0; i < n_pts; ++i) err[i] = std::fabs(Ti[i]) / std::max(1.0, std::fabs(Tv[i]));
+  for (int i = 0; i < n_pts; ++i) {
+    err[i] = std::fabs(Ti[i]) / std::max(1.0, std::fabs(Tv[i]));
+    if (h->mixed() && (int)h->c_err.size() == n_pts && h->c_err[i] >= 0.0) err[i] = std::max(err[i], h->c_err[i]);
+  }
   if (h->cfg.device_ptrs) {
     cudaError_t e = cudaMemcpyAsync(T, Tv.data(), sizeof(double) * n_pts, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && err_est)
@@ -1027,6 +1226,347 @@ int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, d
   return rc;
 }
 
+int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb_out, int* upd_out,
+                double* ms_out) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (s_b < 1 || s_b > h->cfg.s_b_max || n_problems < 1) return fail(h, SS_ERR_ARG, "ss_autotune: bad sizes");
+  const int prec = h->cfg.precision;
+  auto report = [&](const ss_handle::Tune& t) {
+    if (nb_out) *nb_out = t.nb;
+    if (upd_out) *upd_out = t.upd;
+    if (ms_out) *ms_out = t.ms;
+    return SS_OK;
+  };
+  // cache lines: "<precision> <s_b> <n_problems> <nb> <upd> <ms>"
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      int pr, sb, np, nb, upd;
+      double ms;
+      bool hit = false;
+      ss_handle::Tune t{};
+      while (std::fscanf(f, "%d %d %d %d %d %lf", &pr, &sb, &np, &nb, &upd, &ms) == 6)
+        if (pr == prec && sb == s_b && np == n_problems) { t = {nb, upd, ms}; hit = true; }
+      std::fclose(f);
+      if (hit) { h->tune[s_b] = t; return report(t); }
+    }
+  }
+  // synthetic batch of [D | B] systems, D diagonally weighted so the
+  // factorisation is well posed; a pristine copy restores it between runs
+  const size_t per = (size_t)s_b * 2 * s_b;
+  const size_t tot = per * n_problems;
+  z64 *W = nullptr, *W0 = nullptr;
+  int *piv = nullptr, *info = nullptr;
+  cudaStream_t st = h->stream;
+  CK(cudaMalloc(&W, tot * sizeof(z64)), "autotune buffer");
+  cudaError_t e = cudaMalloc(&W0, tot * sizeof(z64));
+  if (e == cudaSuccess) e = cudaMalloc(&piv, (size_t)n_problems * s_b * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&info, (size_t)n_problems * sizeof(int));
+  if (e != cudaSuccess) { cudaFree(W); cudaFree(W0); cudaFree(piv); return cuda_fail(h, e, "autotune buffer"); }
+  {
+    std::vector<z64> host(tot);
+    unsigned long long r = 12345;
+    for (size_t i = 0; i < tot; ++i) {
+      r = r * 6364136223846793005ull + 1442695040888963407ull;
+      const double a = ((double)((r >> 11) & ((1ull << 52) - 1)) / (double)(1ull << 52)) - 0.5;
+      r = r * 6364136223846793005ull + 1442695040888963407ull;
+      const double b = ((double)((r >> 11) & ((1ull << 52) - 1)) / (double)(1ull << 52)) - 0.5;
+      host[i] = make_double2(a, b);
+    }
+    for (int p = 0; p < n_problems; ++p)
+      for (int i = 0; i < s_b; ++i) host[p * per + (size_t)i * 2 * s_b + i].x += 4.0;
+    e = cudaMemcpy(W0, host.data(), tot * sizeof(z64), cudaMemcpyHostToDevice);
+  }
+  std::vector<ss_handle::Tune> cands;
+  const int nbs[2] = {8, s_b <= 512 ? 16 : 32};
+  for (int nb : nbs) {
+    cands.push_back({nb, (int)Plan::UPD_FP64, 0.0});
+    if (h->mixed()) cands.push_back({nb, (int)Plan::UPD_EXACT_TC, 0.0});
+  }
+  ss_handle::Tune best{-1, 0, 0.0};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (auto& c : cands) {
+    if (e != cudaSuccess) break;
+    std::vector<LuDesc> ds;
+    for (int p = 0; p < n_problems; ++p) {
+      LuDesc L{};
+      L.w = W + p * per; L.ldw = 2 * s_b; L.s = s_b; L.ncols = 2 * s_b; L.ipiv = piv + (size_t)p * s_b; L.info = info + p;
+      ds.push_back(L);
+    }
+    Plan P;
+    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err)) continue;
+    e = P.upload(st);
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      e = cudaMemcpyAsync(W, W0, tot * sizeof(z64), cudaMemcpyDeviceToDevice, st);
+      cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = P.run(st, nullptr);
+      cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best_ms = std::min(best_ms, ms);  // first run warms up
+    }
+    c.ms = best_ms;
+    if (e == cudaSuccess && (best.nb < 0 || c.ms < best.ms)) best = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(W); cudaFree(W0); cudaFree(piv); cudaFree(info);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune run");
+  if (best.nb < 0) return fail(h, SS_ERR_OOM, "no candidate fits the packing buffer");
+  h->tune[s_b] = best;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%d %d %d %d %d %.6f\n", prec, s_b, n_problems, best.nb, best.upd, best.ms);
+      std::fclose(f);
+    }
+  }
+  return report(best);
+}
+
+int ss_set_warm_start(ss_handle* h, ss_mlp* net, int side, double out_scale) {
+  if (!h) return SS_ERR_ARG;
+  if (side < 0 || side > 1 || !(out_scale > 0.0)) return fail(h, SS_ERR_ARG, "side must be 0/1, out_scale > 0");
+  h->warm_net[side] = net;
+  h->warm_scale[side] = out_scale;
+  return SS_OK;
+}
+
+int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, const double* kval, int side,
+                  int use_warm, int warm_iters, double warm_tol, ss_c64* g, int* iters, int* seeded, int* status) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (n_pts < 0 || side < 0 || side > 1 || !E || !k_id || !g || warm_iters < 0)
+    return fail(h, SS_ERR_ARG, "ss_surface_gf: bad arguments");
+  if (n_pts == 0) return SS_OK;
+  ss_mlp* net = use_warm ? h->warm_net[side] : nullptr;
+  if (use_warm && !net) return fail(h, SS_ERR_STATE, "no warm-start network attached for this side");
+  if (net && !kval) return fail(h, SS_ERR_ARG, "kval is required with the warm start");
+  int n_in = 0, n_out = 0, mb = 0;
+  if (net) mlp_dims(net, &n_in, &n_out, &mb);
+  const bool dp = h->cfg.device_ptrs != 0;
+  cudaStream_t st = h->stream;
+  const int P_max = h->cfg.max_points;
+  int rc_all = SS_OK;
+  size_t gofs = 0;
+  for (int base = 0; base < n_pts; base += P_max) {
+    const int P = std::min(P_max, n_pts - base);
+    std::vector<PW> pts(P);
+    Carve c(h->arena);
+    int smax = 0;
+    for (int p = 0; p < P; ++p) {
+      auto it = h->ks.find(k_id[base + p]);
+      if (it == h->ks.end()) return fail(h, SS_ERR_STATE, "no Hamiltonian for k_id " + std::to_string(k_id[base + p]));
+      PW& w = pts[p];
+      w.idx = base + p; w.n = it->second.n; w.s = it->second.s; w.E = E[base + p]; w.kd = &it->second;
+      carve_point(c, w, h->cfg.max_inj, h->mixed());
+      smax = std::max(smax, w.s);
+    }
+    if (c.off > h->arena_bytes) return fail(h, SS_ERR_OOM, "workspace too small for the chunk");
+    const int NP = 2 * P;
+    int rc = ensure_scalars(h, 2 * P * 3 + 4 * P, 3 * 2 * P, P);
+    if (rc) return rc;
+    int* act = h->dint;
+    int* itr = act + NP;
+    int* conv = itr + NP;
+    int* dinfo = conv + NP;
+    double* na = h->ddbl;
+    double* nb = na + NP;
+    double* nd = nb + NP;
+    std::vector<int> accepted(P, 0);
+    const double eta = h->cfg.eta;
+    // ---------------- warm start: network seed, fixed-point steps, residual judge
+    if (net) {
+      const int s = pts[0].s;
+      for (auto& w : pts)
+        if (w.s != s || 2 * s * s != n_out) return fail(h, SS_ERR_ARG, "network output does not match s_b");
+      if (P > mb) return fail(h, SS_ERR_ARG, "network max_batch below max_points");
+      const size_t need = (size_t)P_max * (n_in + n_out);
+      if (need > h->warm_cap) {
+        cudaFree(h->feat); cudaFree(h->warm_y); cudaFree(h->wres);
+        h->feat = nullptr; h->warm_y = nullptr; h->wres = nullptr;
+        CK(cudaMalloc(&h->feat, (size_t)P_max * n_in * sizeof(float)), "warm features");
+        CK(cudaMalloc(&h->warm_y, (size_t)P_max * n_out * sizeof(float)), "warm outputs");
+        CK(cudaMalloc(&h->wres, (size_t)P_max * sizeof(double)), "warm residuals");
+        h->warm_cap = need;
+      }
+      std::vector<float> f((size_t)P * n_in, 0.f);
+      for (int p = 0; p < P; ++p) {
+        const double e = E[base + p], k = kval[base + p];
+        float* r = &f[(size_t)p * n_in];
+        r[0] = (float)e; r[1] = (float)std::cos(k); r[2] = (float)std::sin(k);
+        for (int m = 1; m <= 8 && 3 + 2 * m - 1 < n_in; ++m) {
+          r[3 + 2 * (m - 1)] = (float)std::sin(m * M_PI * e);
+          r[4 + 2 * (m - 1)] = (float)std::cos(m * M_PI * e);
+        }
+      }
+      cudaStream_t ns = mlp_stream(net);
+      CK(cudaMemcpyAsync(h->feat, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, ns), "features");
+      int r2 = ss_mlp_forward(net, P, h->feat, h->warm_y);
+      if (r2 != SS_OK) return fail(h, r2, "network forward failed");
+      cudaEvent_t ev;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+      cudaEventRecord(ev, ns);
+      cudaStreamWaitEvent(st, ev, 0);
+      cudaEventDestroy(ev);
+      for (int p = 0; p < P; ++p)
+        launch_unpack_g(h->warm_y + (size_t)p * n_out, s, 1.0 / h->warm_scale[side], pts[p].es[side], s, st);
+      // lead blocks at z and one fixed-point step g <- (D - U g L)^-1 (right) / (D - L g U)^-1 (left)
+      Plan& setup = h->p_setup;
+      setup.clear();
+      std::vector<FormDesc> fl;
+      for (auto& w : pts) {
+        const z64 z = make_double2(w.E, eta);
+        const z64* const* cc = w.kd->cell[side];
+        fl.push_back(fformed(w.D[side], s, cc[2], cc[0], z, s, s, s));
+        fl.push_back(fformed(w.a[side][0], s, cc[3], cc[1], z, s, s, s));
+        fl.push_back(fformed(w.b[side][0], s, cc[3], cc[1], z, s, s, s, 1));
+      }
+      setup.form(fl);
+      Plan& I = h->p_warm_iter;
+      I.clear();
+      std::vector<GemmDesc> g1, g2;
+      std::vector<FormDesc> f1, f2;
+      std::vector<LuDesc> lus;
+      for (int p = 0; p < P; ++p) {
+        PW& w = pts[p];
+        const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
+        const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
+        z64* W = w.Wd[side];
+        g1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
+        f1.push_back(fcopy(W, 2 * s, w.D[side], s, s, s));
+        f1.push_back(fident(W + s, 2 * s, s, s, 1.0));
+        g2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, 2 * s, MONE, ONE));
+        LuDesc L{};
+        L.w = W; L.ldw = 2 * s; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[side]; L.info = dinfo + 2 * p + side;
+        lus.push_back(L);
+        f2.push_back(fcopy(w.es[side], s, W + s, 2 * s, s, s));
+      }
+      I.memset0(dinfo, sizeof(int) * 4 * P);
+      big_gemm(h, I, g1);
+      I.form(f1);
+      big_gemm(h, I, g2);
+      ::lu(h, I, lus);
+      I.form(f2);
+      // judge: ||g (D - U g L) - 1||_F^2 into wres
+      Plan& J = h->p_warm_judge;
+      J.clear();
+      std::vector<GemmDesc> j1, j2, j3;
+      std::vector<FormDesc> jf;
+      std::vector<Norm1Desc> fr;
+      J.memset0(h->wres, sizeof(double) * P);
+      for (int p = 0; p < P; ++p) {
+        PW& w = pts[p];
+        const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
+        const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
+        z64* W = w.Wd[side];
+        j1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
+        jf.push_back(fcopy(W, s, w.D[side], s, s, s));
+        j2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, s, MONE, ONE));
+        GemmDesc q = gdesc(s, s, s, plain(w.es[side], s), plain(W, s), w.T2[side], s, ONE, MONE);
+        q.cmode = 2;
+        j3.push_back(q);
+        fr.push_back({w.T2[side], s, s, s, h->wres + p, nullptr});
+      }
+      // the judge runs in FP64 whatever the precision mode
+      J.gemm(j1);
+      J.form(jf);
+      J.gemm(j2);
+      J.gemm(j3);
+      J.frob2(fr);
+      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small");
+      CK(setup.upload(st), "upload warm");
+      CK(I.upload(st), "upload warm");
+      CK(J.upload(st), "upload warm");
+      CK(setup.run(st, &h->nlaunch, h->P()), "warm setup");
+      for (int it = 0; it < warm_iters; ++it) CK(I.run(st, &h->nlaunch, h->P()), "warm step");
+      CK(J.run(st, &h->nlaunch, h->P()), "warm judge");
+      std::vector<double> res(P);
+      CK(cudaMemcpyAsync(res.data(), h->wres, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read residual");
+      CK(cudaStreamSynchronize(st), "warm sync");
+      for (int p = 0; p < P; ++p)
+        accepted[p] = std::isfinite(res[p]) && std::sqrt(res[p] / (double)s) <= warm_tol ? 1 : 0;
+    }
+    // ---------------- plain doubling for the others (this lead only)
+    std::vector<int> h_it(NP, 0), h_conv(NP, 1), h_dinfo(4 * P, 0), init(NP, 0);
+    bool any = false;
+    for (int p = 0; p < P; ++p)
+      if (!accepted[p]) { init[2 * p + side] = 1; any = true; }
+    if (any) {
+      h->plan_error = false;
+      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd, true);
+      // g = es^-1 for the lead: [es | 1] -> LU
+      Plan& F = h->p_final_g;
+      F.clear();
+      std::vector<FormDesc> ff, fo;
+      std::vector<LuDesc> lus;
+      for (int p = 0; p < P; ++p) {
+        if (accepted[p]) continue;
+        PW& w = pts[p];
+        const int s = w.s;
+        z64* W = w.Wd[side];
+        ff.push_back(fcopy(W, 2 * s, w.es[side], s, s, s));
+        ff.push_back(fident(W + s, 2 * s, s, s, 1.0));
+        LuDesc L{};
+        L.w = W; L.ldw = 2 * s; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[side]; L.info = dinfo + 2 * P + 2 * p + side;
+        lus.push_back(L);
+        fo.push_back(fcopy(w.T1[side], s, W + s, 2 * s, s, s));
+      }
+      F.form(ff);
+      ::lu(h, F, lus);
+      F.form(fo);
+      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small");
+      CK(cudaMemcpyAsync(act, init.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st), "flags");
+      CK(h->p_setup.upload(st), "upload");
+      CK(h->p_iter[0].upload(st), "upload");
+      CK(h->p_iter[1].upload(st), "upload");
+      CK(F.upload(st), "upload");
+      CK(h->p_setup.run(st, &h->nlaunch, h->P()), "setup");
+      std::vector<int> h_act(NP);
+      for (int it = 0; it < h->cfg.decim_max_iter + 2; it += 2) {
+        CK(h->p_iter[0].run(st, &h->nlaunch, h->P()), "doubling step");
+        CK(h->p_iter[1].run(st, &h->nlaunch, h->P()), "doubling step");
+        CK(cudaMemcpyAsync(h_act.data(), act, sizeof(int) * NP, cudaMemcpyDeviceToHost, st), "flags");
+        CK(cudaStreamSynchronize(st), "sync");
+        bool a2 = false;
+        for (int v : h_act) a2 = a2 || v;
+        if (!a2) break;
+      }
+      CK(F.run(st, &h->nlaunch, h->P()), "final g");
+      CK(cudaMemcpyAsync(h_it.data(), itr, sizeof(int) * NP, cudaMemcpyDeviceToHost, st), "iters");
+      CK(cudaMemcpyAsync(h_conv.data(), conv, sizeof(int) * NP, cudaMemcpyDeviceToHost, st), "conv");
+    }
+    CK(cudaMemcpyAsync(h_dinfo.data(), dinfo, sizeof(int) * 4 * P, cudaMemcpyDeviceToHost, st), "info");
+    // outputs
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const size_t cnt = (size_t)w.s * w.s;
+      const z64* src = accepted[p] ? w.es[side] : w.T1[side];
+      CK(cudaMemcpyAsync(g + gofs, src, cnt * sizeof(z64), dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+         "copy g");
+      gofs += cnt;
+    }
+    CK(cudaStreamSynchronize(st), "surface gf sync");
+    if (h->cfg.profile) h->prof.collect();
+    for (int p = 0; p < P; ++p) {
+      int stt = SS_OK;
+      if (!accepted[p]) {
+        if (!h_conv[2 * p + side]) stt = SS_ERR_NOT_CONVERGED;
+        if (h_dinfo[2 * p + side] || h_dinfo[2 * P + 2 * p + side]) stt = SS_ERR_SINGULAR;
+      }
+      if (iters) iters[base + p] = accepted[p] ? warm_iters : h_it[2 * p + side];
+      if (seeded) seeded[base + p] = accepted[p];
+      if (status) status[base + p] = stt;
+      rc_all = worst(rc_all, stt);
+    }
+  }
+  h->c_sigma = h->c_T = false;
+  return rc_all;
+}
+
 int ss_destroy(ss_handle* h) {
   if (!h) return SS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -1038,6 +1578,11 @@ int ss_destroy(ss_handle* h) {
   cudaFree(h->dint);
   cudaFree(h->ddbl);
   cudaFree(h->dtr);
+  cudaFree(h->feat);
+  cudaFree(h->warm_y);
+  cudaFree(h->wres);
+  h->p_warm_iter.clear(); h->p_warm_judge.clear(); h->p_final_g.clear();
+  h->p_ir_res.clear(); h->p_ir_cor.clear();
   h->p_setup.clear(); h->p_iter[0].clear(); h->p_iter[1].clear();
   h->p_final.clear(); h->p_sweep.clear(); h->p_bound.clear();
   h->prof.reset();

@@ -138,7 +138,16 @@ void launch_decim_check(double* na, double* nb, const double* nd, int* act, int*
                         int* conv, int nprob, double tol, int cap, int count, cudaStream_t st);
 
 void launch_fill_i32(int* p, int n, int v, cudaStream_t st);
+
+}  // namespace ss
+struct ss_mlp;
+namespace ss {
+cudaStream_t mlp_stream(const ss_mlp* n);
+void mlp_dims(const ss_mlp* n, int* n_in, int* n_out, int* max_batch);
 void launch_real_part(const z64* in, double* out, int n, cudaStream_t st);
+// out += sum |a|^2 (Norm1Desc reused; *out must start at 0)
+void launch_frob2(const Norm1Desc* d, int nprob, int max_cols, cudaStream_t st);
+void launch_unpack_g(const float* y, int s, double inv_scale, z64* g, int ldg, cudaStream_t st);
 
 // Descriptors of the Caroli trace T = Re Tr[Gamma_L G Gamma_R G^H] for n_pts
 // points of size s, with scratch laid out as [GamL | GamR | M1 | M2] per point

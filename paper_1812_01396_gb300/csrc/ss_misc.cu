@@ -123,6 +123,37 @@ __global__ void decim_check_kernel(double* __restrict__ na, double* __restrict__
   conv[p] = c ? 1 : 0;
   if (c || iters[p] >= cap || m != m || a != a || b != b) act[p] = 0;
 }
+// sum |a_ij|^2 over an m x n block (one CTA per 256 columns, atomic add)
+__global__ void __launch_bounds__(256) frob2_kernel(const Norm1Desc* __restrict__ descs) {
+  const Norm1Desc d = descs[blockIdx.y];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int c = blockIdx.x * 256 + threadIdx.x;
+  double sum = 0.0;
+  if (c < d.cols)
+    for (int r = 0; r < d.rows; ++r) {
+      const z64 v = d.a[(size_t)r * d.lda + c];
+      sum = fma(v.x, v.x, fma(v.y, v.y, sum));
+    }
+  __shared__ double red[8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int q = 0; q < 8; ++q) b += red[q];
+    atomicAdd(d.out, b);
+  }
+}
+
+// g (s x s complex, ld) = (y[0:s^2] + i y[s^2:2s^2]) * inv_scale, y fp32 row-major
+__global__ void unpack_g_kernel(const float* __restrict__ y, int s, double inv_scale, z64* g, int ldg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s * s) return;
+  const int r = i / s, c = i % s;
+  g[(size_t)r * ldg + c] = zmk((double)y[i] * inv_scale, (double)y[(size_t)s * s + i] * inv_scale);
+}
+
 __global__ void real_part_kernel(const z64* __restrict__ in, double* __restrict__ out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[i].x;
@@ -133,6 +164,16 @@ __global__ void fill_i32_kernel(int* p, int n, int v) {
   if (i < n) p[i] = v;
 }
 }  // namespace
+
+void launch_frob2(const Norm1Desc* d, int nprob, int max_cols, cudaStream_t st) {
+  if (nprob <= 0 || max_cols <= 0) return;
+  dim3 grid((max_cols + 255) / 256, nprob);
+  frob2_kernel<<<grid, 256, 0, st>>>(d);
+}
+
+void launch_unpack_g(const float* y, int s, double inv_scale, z64* g, int ldg, cudaStream_t st) {
+  unpack_g_kernel<<<(s * s + 255) / 256, 256, 0, st>>>(y, s, inv_scale, g, ldg);
+}
 
 void launch_real_part(const z64* in, double* out, int n, cudaStream_t st) {
   if (n <= 0) return;

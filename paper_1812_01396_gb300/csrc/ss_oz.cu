@@ -54,6 +54,13 @@ __device__ __forceinline__ double pow2(int e) {
   return ldexp(1.0, e);
 }
 
+// Exponent e with max < 2^e from the IEEE bits of a non-negative maximum
+// (0 for an all-zero vector; subnormal maxima use the smallest normal scale).
+__device__ __forceinline__ int exp_of(unsigned long long mx) {
+  const int ex = (int)(mx >> 52);
+  return mx == 0 ? 0 : (ex == 0 ? -1021 : ex - 1022);
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __restrict__ descs,
                                                                 const int* __restrict__ tile_start, int nprob,
                                                                 int* err) {
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
   }
   if (threadIdx.x < BN / 2) {
     const int j = (n0 >> 1) + threadIdx.x;
-    colscale[threadIdx.x] = (2 * j < d.n2) ? pow2(d.eB[j]) : 0.0;
+    colscale[threadIdx.x] = (2 * j < d.n2) ? pow2(exp_of(d.mB[j])) : 0.0;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -201,7 +208,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
     }
     if (ok && !s_fail && row < d.m) {
       // value = fixed / 2^37 * 2^{-2 beta} * 2^{eA[row]} * 2^{eB[j]}
-      const double rs_row = pow2(d.eA[row] - 37 - 2 * d.beta_bits);
+      const double rs_row = pow2(exp_of(d.mA[row]) - 37 - 2 * d.beta_bits);
       const bool unit_alpha = d.alpha.y == 0.0 && (d.alpha.x == 1.0 || d.alpha.x == -1.0);
 #pragma unroll
       for (int e = 0; e < BN / 2; ++e) {
@@ -240,35 +247,48 @@ __device__ __forceinline__ z64 oz_load(const OzPackDesc& p, int i, int j) {
   return p.trans ? zconj(v) : v;
 }
 
-// Exponent e with max |entry| < 2^e over one row of op(A) (role 0) or one
-// column of op(B) (role 1); 0 for an all-zero vector.  One warp per vector;
-// the maximum is taken on the IEEE bits of |x| (monotone for non-negative).
-__global__ void oz_scale_kernel(const OzPackDesc* __restrict__ descs, const int* __restrict__ tile_start,
-                                int nprob) {
+// The (vector, inner) index of op(X): vector = row of op(A) (role 0) or
+// column of op(B) (role 1).  `contig_inner` tells which index runs along
+// memory, so tiles are loaded with consecutive threads on consecutive
+// addresses whatever the operand's orientation.
+__device__ __forceinline__ bool contig_inner(const OzPackDesc& p) {
+  return (p.role == 0 && !p.trans) || (p.role == 1 && p.trans);
+}
+__device__ __forceinline__ z64 oz_elem(const OzPackDesc& p, int v, int kk) {
+  return p.role == 0 ? oz_load(p, v, kk) : oz_load(p, kk, v);
+}
+
+// Per-vector maximum of max(|re|, |im|) over a 32 x 32 tile, merged with
+// an integer atomicMax on the IEEE bits (monotone for non-negative values).
+__global__ void __launch_bounds__(256) oz_scale_kernel(const OzPackDesc* __restrict__ descs,
+                                                       const int* __restrict__ tile_start, int nprob) {
   const int pid = find_problem(tile_start, nprob, blockIdx.x);
   const OzPackDesc& p = descs[pid];
   if (p.active && __ldg(p.active) == 0) return;
-  const int v = (blockIdx.x - __ldg(tile_start + pid)) * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   const int nvec = p.role == 0 ? p.rows : p.rows / 2;
-  if (v >= nvec) return;
-  unsigned long long mx = 0;
-  for (int kk = lane; kk < p.k; kk += 32) {
-    const z64 z = p.role == 0 ? oz_load(p, v, kk) : oz_load(p, kk, v);
-    const unsigned long long a = (unsigned long long)__double_as_longlong(z.x) & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(z.y) & 0x7FFFFFFFFFFFFFFFull;
-    mx = a > mx ? a : mx;
-    mx = b > mx ? b : mx;
+  const int kt = (p.k + 31) / 32;
+  const int t = blockIdx.x - __ldg(tile_start + pid);
+  const int v0 = (t / kt) * 32, k0 = (t % kt) * 32;
+  __shared__ unsigned long long tile[32][33];
+  const bool ci = contig_inner(p);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    const int a = e / 32, b = e % 32;  // b runs along memory
+    const int v = v0 + (ci ? a : b), kk = k0 + (ci ? b : a);
+    unsigned long long m = 0;
+    if (v < nvec && kk < p.k) {
+      const z64 z = oz_elem(p, v, kk);
+      const unsigned long long x = (unsigned long long)__double_as_longlong(z.x) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long y = (unsigned long long)__double_as_longlong(z.y) & 0x7FFFFFFFFFFFFFFFull;
+      m = x > y ? x : y;
+    }
+    tile[ci ? a : b][ci ? b : a] = m;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long q = __shfl_down_sync(0xffffffffu, mx, o);
-    mx = q > mx ? q : mx;
-  }
-  if (lane == 0) {
-    const int ex = (int)(mx >> 52);
-    // normal: |x| = f 2^(ex-1022), f in [0.5, 1); subnormal rows use the smallest normal scale
-    p.exps[v] = mx == 0 ? 0 : (ex == 0 ? -1021 : ex - 1022);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int v = v0 + threadIdx.x;
+    unsigned long long m = 0;
+    for (int j = 0; j < 32; ++j) m = tile[threadIdx.x][j] > m ? tile[threadIdx.x][j] : m;
+    if (v < nvec && m) atomicMax(p.maxb + v, m);
   }
 }
 
@@ -295,43 +315,76 @@ __device__ __forceinline__ void write_digits(__nv_bfloat16* row, int w, int off,
   }
 }
 
-__global__ void oz_pack_kernel(const OzPackDesc* __restrict__ descs, const int* __restrict__ tile_start,
-                               int nprob) {
+// Digit slices of a 32 x 32 tile (coalesced loads into shared memory, then
+// rows of the packed matrix written along the inner index), or, for the
+// tiles past the data, the zero padding of every slice.
+__global__ void __launch_bounds__(256) oz_pack_kernel(const OzPackDesc* __restrict__ descs,
+                                                      const int* __restrict__ tile_start, int nprob) {
   const int pid = find_problem(tile_start, nprob, blockIdx.x);
   const OzPackDesc& p = descs[pid];
   if (p.active && __ldg(p.active) == 0) return;
-  const int wtiles = (p.w + 255) / 256;
-  const int tt = blockIdx.x - __ldg(tile_start + pid);
-  const int r = tt / wtiles;
-  const int off = (tt % wtiles) * 256 + threadIdx.x;
-  if (r >= p.rows || off >= p.w) return;
-  __nv_bfloat16* row = p.out + (size_t)r * p.S * p.w;
+  const int nvec = p.role == 0 ? p.rows : p.rows / 2;
   const int k = p.k;
-  if (off >= 2 * k) {
-    for (int t = 0; t < p.S; ++t) row[(size_t)t * p.w + off] = __double2bfloat16(0.0);
+  const int kt = (k + 31) / 32, pt = (p.w - 2 * k + 31) / 32;
+  const int t = blockIdx.x - __ldg(tile_start + pid);
+  const int v0 = (t / (kt + pt)) * 32, ti = t % (kt + pt);
+  const int nrow_per_vec = p.role == 0 ? 1 : 2;
+  const size_t rowlen = (size_t)p.S * p.w;
+  if (ti >= kt) {  // zero padding columns [2k + 32 (ti - kt), ...)
+    const int c0 = 2 * k + 32 * (ti - kt);
+    for (int e = threadIdx.x; e < 32 * 32 * nrow_per_vec; e += 256) {
+      const int c = c0 + (e % 32), vr = e / 32;
+      const int v = v0 + vr / nrow_per_vec;
+      if (v >= nvec || c >= p.w) continue;
+      const int row = p.role == 0 ? v : 2 * v + (vr % 2);
+      for (int s = 0; s < p.S; ++s) p.out[(size_t)row * rowlen + (size_t)s * p.w + c] = __double2bfloat16(0.0);
+    }
     return;
   }
-  const int kk = off < k ? off : off - k;
-  double x;
-  int e;
-  if (p.role == 0) {  // A' row r = [Ar | Ai]
-    const z64 v = oz_load(p, r, kk);
-    x = off < k ? v.x : v.y;
-    e = p.exps[r];
-  } else {  // B' rows 2j = [Br | -Bi], 2j+1 = [Bi | Br]
-    const int j = r >> 1;
-    const z64 v = oz_load(p, kk, j);
-    if ((r & 1) == 0) x = off < k ? v.x : -v.y;
-    else x = off < k ? v.y : v.x;
-    e = p.exps[j];
+  const int k0 = ti * 32;
+  __shared__ z64 tile[32][33];
+  __shared__ int ex[32];
+  const bool ci = contig_inner(p);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    const int a = e / 32, b = e % 32;
+    const int vv = ci ? a : b, kk = ci ? b : a;
+    const int v = v0 + vv, kg = k0 + kk;
+    tile[vv][kk] = (v < nvec && kg < k) ? oz_elem(p, v, kg) : zmk(0.0, 0.0);
   }
-  write_digits(row, p.w, off, p.S, p.beta_bits, x, e);
+  if (threadIdx.x < 32) ex[threadIdx.x] = v0 + threadIdx.x < nvec ? exp_of(p.maxb[v0 + threadIdx.x]) : 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    const int vv = e / 32, kk = e % 32;
+    const int v = v0 + vv, kg = k0 + kk;
+    if (v >= nvec || kg >= k) continue;
+    const z64 z = tile[vv][kk];
+    if (p.role == 0) {  // A' row v = [Ar | Ai]
+      __nv_bfloat16* row = p.out + (size_t)v * rowlen;
+      write_digits(row, p.w, kg, p.S, p.beta_bits, z.x, ex[vv]);
+      write_digits(row, p.w, k + kg, p.S, p.beta_bits, z.y, ex[vv]);
+    } else {  // B' rows 2v = [Br | -Bi], 2v+1 = [Bi | Br]
+      __nv_bfloat16* r0 = p.out + (size_t)(2 * v) * rowlen;
+      __nv_bfloat16* r1 = r0 + rowlen;
+      write_digits(r0, p.w, kg, p.S, p.beta_bits, z.x, ex[vv]);
+      write_digits(r0, p.w, k + kg, p.S, p.beta_bits, -z.y, ex[vv]);
+      write_digits(r1, p.w, kg, p.S, p.beta_bits, z.y, ex[vv]);
+      write_digits(r1, p.w, k + kg, p.S, p.beta_bits, z.x, ex[vv]);
+    }
+  }
 }
 
 }  // namespace
 
 size_t oz_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
 int oz_tiles(int m, int n2) { return ((m + BM - 1) / BM) * ((n2 + BN - 1) / BN); }
+int oz_scale_tiles(const OzPackDesc& d) {
+  const int nvec = d.role == 0 ? d.rows : d.rows / 2;
+  return ((nvec + 31) / 32) * ((d.k + 31) / 32);
+}
+int oz_pack_tiles(const OzPackDesc& d) {
+  const int nvec = d.role == 0 ? d.rows : d.rows / 2;
+  return ((nvec + 31) / 32) * ((d.k + 31) / 32 + (d.w - 2 * d.k + 31) / 32);
+}
 int oz_box_rows_a() { return BM; }
 int oz_box_rows_b() { return BN; }
 

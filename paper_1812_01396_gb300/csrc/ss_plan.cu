@@ -22,7 +22,7 @@ namespace {
 size_t oz_operand_bytes(int rows, int vecs, int k) {
   OzShape sh;
   oz_plan(k, &sh);
-  return al1k((size_t)rows * sh.S * sh.w * 2) + al1k((size_t)vecs * sizeof(int));
+  return al1k((size_t)rows * sh.S * sh.w * 2) + al1k((size_t)vecs * sizeof(unsigned long long));
 }
 }  // namespace
 
@@ -38,7 +38,7 @@ size_t Plan::oz_pack_bytes(const std::vector<GemmDesc>& ds) {
   return tot;
 }
 
-bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err) {
+bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label) {
   if (ds.empty()) return true;
   std::map<OpKey, int> index;
   std::vector<OzPackDesc> pk;
@@ -60,13 +60,13 @@ bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t 
       int mi;
       if (it == index.end()) {
         const size_t bytes = al1k((size_t)rows * sh.S * sh.w * 2);
-        const size_t ebytes = al1k((size_t)vecs * sizeof(int));
+        const size_t ebytes = al1k((size_t)vecs * sizeof(unsigned long long));
         if (used + bytes + ebytes > cap) return false;
         OzPackDesc d{};
         d.x = o.p; d.s = o.s; d.e = o.e; d.ld = o.ld; d.trans = o.trans; d.role = role;
         d.rows = rows; d.k = g.k; d.w = sh.w; d.S = sh.S; d.beta_bits = sh.beta;
         d.out = reinterpret_cast<__nv_bfloat16*>(pack + used);
-        d.exps = reinterpret_cast<int*>(pack + used + bytes);
+        d.maxb = reinterpret_cast<unsigned long long*>(pack + used + bytes);
         d.active = g.active;
         CUtensorMap m;
         if (encode_kmajor_map(&m, pack + used, rows, sh.S * sh.w, role == 0 ? oz_box_rows_a() : oz_box_rows_b()) !=
@@ -83,14 +83,17 @@ bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t 
       (role == 0 ? amap : bmap)[i] = mi;
     }
   }
-  // exponents, then digit slices
+  // maxima (zeroed first), then digit slices
   {
+    for (auto& d : pk) {
+      const int nvec = d.role == 0 ? d.rows : d.rows / 2;
+      memset0(d.maxb, (size_t)nvec * sizeof(unsigned long long));
+    }
     std::vector<int> start(pk.size());
     int tot = 0;
     for (size_t i = 0; i < pk.size(); ++i) {
       start[i] = tot;
-      const int nvec = pk[i].role == 0 ? pk[i].rows : pk[i].rows / 2;
-      tot += (nvec + 7) / 8;  // one warp per vector, 8 warps per block
+      tot += oz_scale_tiles(pk[i]);
     }
     const size_t off = push_vec(pk);
     LaunchRec r;
@@ -98,7 +101,7 @@ bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t 
     recs_.push_back(r);
     std::vector<int> start2(pk.size());
     int tot2 = 0;
-    for (size_t i = 0; i < pk.size(); ++i) { start2[i] = tot2; tot2 += pk[i].rows * ((pk[i].w + 255) / 256); }
+    for (size_t i = 0; i < pk.size(); ++i) { start2[i] = tot2; tot2 += oz_pack_tiles(pk[i]); }
     LaunchRec r2;
     r2.kind = K_OZPACK; r2.off = off; r2.toff = push_vec(start2); r2.nprob = (int)pk.size(); r2.tiles = tot2;
     recs_.push_back(r2);
@@ -112,8 +115,8 @@ bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t 
     OzDesc t{};
     t.m = g.m; t.n2 = 2 * g.n; t.w = sh.w; t.kc = g.k; t.beta_bits = sh.beta; t.npass = sh.npass;
     for (int p = 0; p < sh.npass; ++p) { t.pd[p] = sh.pd[p]; t.pt0[p] = sh.pt0[p]; t.pnp[p] = sh.pnp[p]; }
-    t.eA = pk[amap[i]].exps;
-    t.eB = pk[bmap[i]].exps;
+    t.mA = pk[amap[i]].maxb;
+    t.mB = pk[bmap[i]].maxb;
     t.c = g.c; t.ldc = g.ldc; t.cmode = g.cmode; t.alpha = g.alpha; t.beta = g.beta;
     t.cs = g.cs; t.ch = g.ch; t.ce = g.ce; t.ldcf = g.ldcf; t.active = g.active;
     ods[i] = t;
@@ -128,7 +131,8 @@ bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t 
   }
   std::memcpy(host_.data() + doff, ods.data(), ods.size() * sizeof(OzDesc));
   LaunchRec r;
-  r.kind = K_OZGEMM; r.off = doff; r.toff = push_vec(start); r.nprob = (int)ds.size(); r.tiles = tot;
+  r.kind = lu_label ? K_OZGEMM_LU : K_OZGEMM; r.off = doff; r.toff = push_vec(start); r.nprob = (int)ds.size();
+  r.tiles = tot;
   r.p[0] = err;
   recs_.push_back(r);
   return true;
@@ -238,8 +242,8 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
-    if (upd == UPD_EXACT_TC) ok = ok && oz_gemm(g, pack, cap, err);
-    else gemm(g, upd == UPD_FP32);
+    if (upd == UPD_EXACT_TC) ok = ok && oz_gemm(g, pack, cap, err, true);
+    else gemm(g, upd == UPD_FP32, upd == UPD_FP64);
   };
   const size_t off = push_vec(ds);
   const int np = (int)ds.size();
@@ -356,11 +360,11 @@ static double oz_issued(const LaunchRec& r, const std::vector<unsigned char>& ho
 
 static double gemm_flops(const LaunchRec& r, const std::vector<unsigned char>& host, const Prof* prof) {
   double f = 0.0;
-  if (r.kind == K_GEMM || r.kind == K_GEMM32) {
+  if (r.kind == K_GEMM || r.kind == K_GEMM32 || r.kind == K_GEMM_LU) {
     const GemmDesc* g = reinterpret_cast<const GemmDesc*>(host.data() + r.off);
     for (int i = 0; i < r.nprob; ++i)
       if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)g[i].n * g[i].k;
-  } else if (r.kind == K_OZGEMM) {
+  } else if (r.kind == K_OZGEMM || r.kind == K_OZGEMM_LU) {
     const OzDesc* g = reinterpret_cast<const OzDesc*>(host.data() + r.off);
     for (int i = 0; i < r.nprob; ++i)
       if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)(g[i].n2 / 2) * (double)g[i].kc;
@@ -379,10 +383,11 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     Prof::Rec pr{};
     if (prof && r.kind != K_MEMSET) {
       pr.kind = r.kind;
-      pr.flops = (r.kind == K_GEMM || r.kind == K_TCGEMM || r.kind == K_GEMM32 || r.kind == K_OZGEMM)
+      pr.flops = (r.kind == K_GEMM || r.kind == K_TCGEMM || r.kind == K_GEMM32 || r.kind == K_OZGEMM ||
+                  r.kind == K_GEMM_LU || r.kind == K_OZGEMM_LU)
                      ? gemm_flops(r, host_, prof)
                      : 0.0;
-      pr.issued = r.kind == K_OZGEMM ? oz_issued(r, host_, prof) : 0.0;
+      pr.issued = (r.kind == K_OZGEMM || r.kind == K_OZGEMM_LU) ? oz_issued(r, host_, prof) : 0.0;
       cudaEventCreate(&pr.a);
       cudaEventCreate(&pr.b);
       cudaEventRecord(pr.a, st);
@@ -390,10 +395,12 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     unsigned char* d = dev_ + r.off;
     const int* t = reinterpret_cast<const int*>(dev_ + r.toff);
     switch (r.kind) {
-      case K_GEMM: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_GEMM:
+      case K_GEMM_LU: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_OZSCALE: launch_oz_scale((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_OZPACK: launch_oz_pack((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
-      case K_OZGEMM: {
+      case K_OZGEMM:
+      case K_OZGEMM_LU: {
         cudaError_t e = launch_oz_gemm((const OzDesc*)d, t, r.nprob, r.tiles, (int*)r.p[0], st);
         if (e != cudaSuccess) return e;
         ++n;
@@ -406,6 +413,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
         if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; }
         break;
       case K_LU_BACK: launch_lu_backsub_diag((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
+      case K_FROB2: launch_frob2((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;
       case K_NORM1: launch_norm1((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;
       case K_TRACE: launch_trace((const TraceDesc*)d, r.nprob, st); ++n; break;
       case K_CHECK:

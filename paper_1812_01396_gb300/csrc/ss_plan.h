@@ -15,7 +15,8 @@ namespace ss {
 
 // Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
 enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
-                  K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_OZSCALE, K_OZPACK, K_OZGEMM, K_MEMSET };
+                  K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_OZSCALE, K_OZPACK, K_OZGEMM, K_FROB2,
+                  K_GEMM_LU, K_OZGEMM_LU, K_MEMSET };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -79,14 +80,15 @@ class Plan {
   size_t push_vec(const std::vector<D>& v, size_t align = 16) { return push(v.data(), v.size() * sizeof(D), align); }
 
   // fp32 = true: the FP32-arithmetic kernel (low-rank updates of the mixed path)
-  void gemm(const std::vector<GemmDesc>& ds, bool fp32 = false) {
+  // lu_label: account the launch as an LU update (profiling only)
+  void gemm(const std::vector<GemmDesc>& ds, bool fp32 = false, bool lu_label = false) {
     if (ds.empty()) return;
     std::vector<int> start(ds.size());
     int tot = 0;
     for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zgemm_tiles(ds[i].m, ds[i].n); }
     if (tot == 0) return;
     LaunchRec r;
-    r.kind = fp32 ? K_GEMM32 : K_GEMM;
+    r.kind = fp32 ? K_GEMM32 : (lu_label ? K_GEMM_LU : K_GEMM);
     r.off = push_vec(ds);
     r.toff = push_vec(start);
     r.nprob = (int)ds.size();
@@ -116,7 +118,7 @@ class Plan {
   static size_t tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode);
   // FP64-accurate complex GEMMs on the tensor cores (digit-sliced BF16, exact
   // FP32 accumulation); operands sliced into `pack` as for tc_gemm.
-  bool oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err);
+  bool oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label = false);
   static size_t oz_pack_bytes(const std::vector<GemmDesc>& ds);
   // Blocked LU + solve of every problem in ds (panel width nb <= 32; nb <= 0
   // picks the width from the largest block of the group).
@@ -130,6 +132,15 @@ class Plan {
     if (ds.empty()) return;
     LaunchRec r;
     r.kind = K_NORM1;
+    r.off = push_vec(ds);
+    r.nprob = (int)ds.size();
+    for (auto& d : ds) r.maxc = d.cols > r.maxc ? d.cols : r.maxc;
+    recs_.push_back(r);
+  }
+  void frob2(const std::vector<Norm1Desc>& ds) {
+    if (ds.empty()) return;
+    LaunchRec r;
+    r.kind = K_FROB2;
     r.off = push_vec(ds);
     r.nprob = (int)ds.size();
     for (auto& d : ds) r.maxc = d.cols > r.maxc ? d.cols : r.maxc;

@@ -59,7 +59,7 @@ struct OzPackDesc {
   z64 e;
   int ld, trans, role;
   int rows, k, w, S, beta_bits;
-  int* exps;            // per-vector exponents (m or n entries)
+  unsigned long long* maxb;  // per-vector max |entry| as IEEE bits (zeroed before the scale pass)
   __nv_bfloat16* out;   // rows x (S * w) row-major
   const int* active;
 };
@@ -68,8 +68,8 @@ struct OzDesc {
   long long ta_off, tb_off;  // tensor maps, relative to the start of the OzDesc array
   int m, n2, w, kc, beta_bits, npass;
   unsigned char pd[OZ_MAXPASS], pt0[OZ_MAXPASS], pnp[OZ_MAXPASS];
-  const int* eA;
-  const int* eB;
+  const unsigned long long* mA;  // row maxima of op(A) (IEEE bits)
+  const unsigned long long* mB;  // column maxima of op(B)
   z64* c;
   int ldc;
   int cmode;
@@ -85,6 +85,9 @@ size_t oz_smem_bytes();
 int oz_tiles(int m, int n2);
 int oz_box_rows_a();
 int oz_box_rows_b();
+// tiles of 32 vectors x 32 inner indices; pack also covers the zero padding
+int oz_scale_tiles(const OzPackDesc& d);
+int oz_pack_tiles(const OzPackDesc& d);
 void launch_oz_scale(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st);
 void launch_oz_pack(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st);
 cudaError_t launch_oz_gemm(const OzDesc* d, const int* tile_start, int nprob, int total, int* err,

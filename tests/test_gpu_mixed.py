@@ -60,3 +60,28 @@ def test_low_precision_modes_rejected_by_pipeline(ss):
     with pytest.raises(ss.SSError) as e:
         ss.Handle(n_b_max=4, s_b_max=32, max_points=1, precision=ss.SS_MIXED_BF16X3)
     assert e.value.code == ss.SS_ERR_ARG
+
+
+def test_refinement_residual_reported_and_small(ss):
+    """Mixed ss_solve refines x in FP64; ss_transmission reports the residual."""
+    dev = synth.make_device(6, 96, seed=44)[0]
+    Es = [0.25, -0.5]
+    inj = [synth.make_injection(96, 4, seed=i)[0] for i in range(2)]
+    h = ss.Handle(n_b_max=6, s_b_max=96, max_points=2, max_inj=4, precision=ss.SS_MIXED_OZAKI)
+    try:
+        h.set_device(0, dev)
+        sL, sR, _, _, _ = h.self_energy(Es, [0, 0])
+        xs, st, _ = h.solve(Es, [0, 0], inj)
+        T, err, st2, _ = h.transmission(Es, [0, 0])
+    finally:
+        h.close()
+    for p in range(2):
+        # the residual of the refined x against the system with the GPU's own
+        # self-energies (the oracle's differ by the doubling's conditioning)
+        M = dense.system_matrix(dev, Es[p], sL[p], sR[p])
+        b = dense.full_injection(inj[p], dev.n_b, dev.s_b)
+        res = dense.residual(M, xs[p], b)
+        assert res < 1e-12, res
+        assert 0.0 <= err[p] < 1e-12
+        assert abs(err[p] - res) < 1e-13 + 0.5 * res
+        check_point({"sL": sL, "sR": sR, "T": T, "x": xs}, p, dev, Es[p], inj[p])

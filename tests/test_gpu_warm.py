@@ -1,0 +1,126 @@
+"""Learned warm start: the network kernels against the FP64 oracle MLP, and
+the warm-started surface Green's function against plain doubling.
+
+Bars: forward and gradients within 1e-2 (relative, per tensor) of the FP64
+oracle run with the same BF16-rounded weights and inputs (the kernels keep
+activations in BF16 and accumulate in FP32).  Every warm-start result equals
+the plain doubling to the conditioning bar: accepted seeds satisfy the FP64
+Dyson residual test, rejected ones fall back to the doubling itself.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ss():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1812_01396_gb300 as mod
+    return mod
+
+
+def bf16(a):
+    """Round float32 to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_mlp_forward_and_gradients_match_oracle(ss):
+    import torch
+    from paper_1812_01396_gb300 import warm
+    net = ss.MLP(19, 48, 32, 16, seed=3)
+    params = [p.astype(np.float32) for p in omlp.init_params(32, width=48, seed=4)]
+    params = [p + 0.05 * np.float32(i % 2) for i, p in enumerate(params)]   # non-zero biases
+    net.set_params(params)
+    rng = np.random.default_rng(2)
+    E, k = rng.uniform(-1, 1, 12), rng.uniform(0, np.pi, 12)
+    x = warm.features(E, k)
+    t = rng.standard_normal((12, 32)).astype(np.float32)
+    tx, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = net.forward(tx).cpu().numpy()
+    net.train_step(tx, tt, 0.0)
+    grads = net.get_grads()
+    op = [bf16(p) if i % 2 == 0 else p.astype(np.float64) for i, p in enumerate(params)]
+    yo, cache = omlp.forward(op, bf16(x))
+    go = omlp.backward(op, cache, yo, t.astype(np.float64))
+    assert rel(y, yo) < 1e-2
+    for i in range(6):
+        assert rel(grads[i], go[i]) < 1e-2, (i, rel(grads[i], go[i]))
+
+
+def test_mlp_training_reduces_loss(ss):
+    import torch
+    from paper_1812_01396_gb300 import warm
+    net = ss.MLP(19, 64, 16, 64, seed=1)
+    rng = np.random.default_rng(0)
+    E = rng.uniform(-1, 1, 64)
+    x = torch.from_numpy(warm.features(E, np.zeros(64))).cuda()
+    t = torch.from_numpy(np.stack([np.sin(3 * E + j) for j in range(16)], 1).astype(np.float32)).cuda()
+    l0 = net.train_step(x, t, 0.0)
+    for _ in range(200):
+        net.train_step(x, t, 3e-3)
+    l1 = net.train_step(x, t, 0.0)
+    assert l1 < 0.2 * l0
+
+
+def test_warm_start_workload_report(ss, capsys):
+    """Lead s_b = 128, 4096 training (E, k) points, 1024 evaluation energies at k = 0."""
+    import torch
+    from paper_1812_01396_gb300 import warm
+    s, nk = 128, 16
+    kgrid = np.linspace(0.0, np.pi, nk, endpoint=False)
+    devs = synth.make_device(2, s, seed=5, k_points=kgrid, w_scale=0.25)
+    h = ss.Handle(n_b_max=2, s_b_max=s, max_points=64, max_inj=1)
+    try:
+        for i, d in enumerate(devs):
+            h.set_device(i, d)
+        rng = np.random.default_rng(7)
+        n_train = 4096
+        Etr = rng.uniform(-1, 1, n_train)
+        ktr_id = rng.integers(0, nk, n_train)
+        t0 = time.time()
+        g_probe, _, _, _, _ = h.surface_gf(Etr[:64], ktr_id[:64], side=1)
+        scale = 1.0 / float(np.sqrt(np.mean([np.mean(np.abs(g) ** 2) for g in g_probe])))
+        net = ss.MLP(warm.N_IN, 512, 2 * s * s, 256, seed=11)
+        losses, _ = warm.train(net, h, Etr, ktr_id, kgrid[ktr_id], 1, scale, epochs=40, batch=256, lr=1e-3)
+        t_train = time.time() - t0
+        h.set_warm_start(net, 1, scale)
+        Ev = -1.0 + (2 * np.arange(1024) + 1) / 1024.0
+        kid = np.zeros(1024, np.int32)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
+        t_plain = time.time() - t0
+        t0 = time.time()
+        g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(1024), side=1, use_warm=True, warm_iters=8,
+                                               warm_tol=1e-10)
+        t_warm = time.time() - t0
+    finally:
+        h.close()
+    errs = np.array([rel(a, b) for a, b in zip(g1, g0)])
+    acc = seeded.astype(bool)
+    # accepted seeds satisfy the Dyson residual test; rejected ones are the doubling itself
+    assert np.all(errs[~acc] == 0.0)
+    if acc.any():
+        assert np.max(errs[acc]) < 1e-6
+    report = dict(train_points=n_train, train_seconds=round(t_train, 2), final_loss=losses[-1], first_loss=losses[0],
+                  eval_points=1024, accepted=int(acc.sum()), mean_iters_plain=float(it0.mean()),
+                  mean_iters_warm=float(np.where(acc, it1, it0 + 8).mean()), t_plain_s=round(t_plain, 3),
+                  t_warm_s=round(t_warm, 3), gain_time=round(t_plain / t_warm, 3))
+    with capsys.disabled():
+        print("\nwarm-start report:", report)
+    assert losses[-1] < losses[0]
