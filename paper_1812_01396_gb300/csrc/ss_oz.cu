@@ -61,9 +61,25 @@ __device__ __forceinline__ int exp_of(unsigned long long mx) {
   return mx == 0 ? 0 : (ex == 0 ? -1021 : ex - 1022);
 }
 
+// Persistent: CTA c processes tiles c, c + gridDim.x, ...  The three roles
+// walk the same tile sequence; the stage ring (producer -> MMA) and the
+// accumulator ring (MMA -> epilogue) continue across tiles, so the epilogue
+// of one tile overlaps the MMAs of the next, and TMEM is allocated once.
+__device__ __forceinline__ bool oz_tile(const OzDesc* __restrict__ descs, const int* __restrict__ tile_start,
+                                        int nprob, int tile, int& pid, int& m0, int& n0) {
+  pid = find_problem(tile_start, nprob, tile);
+  const OzDesc& d = descs[pid];
+  if (d.active && __ldg(d.active) == 0) return false;
+  const int tiles_n = (d.n2 + BN - 1) / BN;
+  const int t = tile - __ldg(tile_start + pid);
+  m0 = (t / tiles_n) * BM;
+  n0 = (t % tiles_n) * BN;
+  return true;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __restrict__ descs,
                                                                 const int* __restrict__ tile_start, int nprob,
-                                                                int* err) {
+                                                                int total_tiles, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -72,30 +88,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
   __shared__ __align__(8) uint64_t accf_bar[NACC];
   __shared__ __align__(8) uint64_t acce_bar[NACC];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
   __shared__ double colscale[BN / 2];
 
-  const int pid = find_problem(tile_start, nprob, blockIdx.x);
-  const OzDesc& d = descs[pid];
-  if (d.active && __ldg(d.active) == 0) return;
-  const CUtensorMap* map_a = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.ta_off);
-  const CUtensorMap* map_b = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.tb_off);
-  const int tiles_n = (d.n2 + BN - 1) / BN;
-  const int t = blockIdx.x - __ldg(tile_start + pid);
-  const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-  const int wt = d.w / BK;  // K-tiles per slice
-  const int npass = d.npass;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
     for (int i = 0; i < NACC; ++i) { mbar_init(&accf_bar[i], 1); mbar_init(&acce_bar[i], 128); }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (threadIdx.x < BN / 2) {
-    const int j = (n0 >> 1) + threadIdx.x;
-    colscale[threadIdx.x] = (2 * j < d.n2) ? pow2(exp_of(d.mB[j])) : 0.0;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -109,126 +110,151 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
   const uint32_t tmem = tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: K-tiles of every pass, in order
+    // ---- TMA producer
     int kt = 0;
-    bool ok = true;
-    for (int p = 0; p < npass && ok; ++p) {
-      const int lev = d.pd[p], t0 = d.pt0[p], np = d.pnp[p];
-      for (int q = 0; q < np && ok; ++q) {
-        const int ta = t0 + q, tb = lev - ta;
-        for (int kk = 0; kk < wt; ++kk, ++kt) {
-          const int st = kt % STAGES;
-          const uint32_t ph = (kt / STAGES) & 1;
-          if (!mbar_wait(&empty_bar[st], ph ^ 1)) { s_fail = 1; ok = false; break; }
-          unsigned char* sa = smem + st * STAGE_BYTES;
-          unsigned char* sb = sa + A_BYTES;
-          mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-          tma_load_2d(sa, map_a, &full_bar[st], ta * d.w + kk * BK, m0);
-          tma_load_2d(sb, map_b, &full_bar[st], tb * d.w + kk * BK, n0);
+    for (int tile = blockIdx.x; tile < total_tiles && !s_fail; tile += gridDim.x) {
+      int pid, m0, n0;
+      if (!oz_tile(descs, tile_start, nprob, tile, pid, m0, n0)) continue;
+      const OzDesc& d = descs[pid];
+      const CUtensorMap* map_a = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.ta_off);
+      const CUtensorMap* map_b = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(descs) + d.tb_off);
+      const int wt = d.w / BK;
+      for (int p = 0; p < d.npass && !s_fail; ++p) {
+        const int lev = d.pd[p], t0 = d.pt0[p], np = d.pnp[p];
+        for (int q = 0; q < np && !s_fail; ++q) {
+          const int ta = t0 + q, tb = lev - ta;
+          for (int kk = 0; kk < wt; ++kk, ++kt) {
+            const int st = kt % STAGES;
+            const uint32_t ph = (kt / STAGES) & 1;
+            if (!mbar_wait(&empty_bar[st], ph ^ 1)) { s_fail = 1; break; }
+            unsigned char* sa = smem + st * STAGE_BYTES;
+            unsigned char* sb = sa + A_BYTES;
+            mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+            tma_load_2d(sa, map_a, &full_bar[st], ta * d.w + kk * BK, m0);
+            tma_load_2d(sb, map_b, &full_bar[st], tb * d.w + kk * BK, n0);
+          }
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: one accumulator of the ring per pass
-    int kt = 0;
-    bool ok = true;
-    for (int p = 0; p < npass; ++p) {
-      const int acc = p % NACC, use = p / NACC;
-      if (ok && !mbar_wait(&acce_bar[acc], (use & 1) ^ 1)) { ok = false; s_fail = 1; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int nk = d.pnp[p] * wt;
-      for (int i = 0; i < nk && ok; ++i, ++kt) {
-        const int st = kt % STAGES;
-        const uint32_t ph = (kt / STAGES) & 1;
-        if (!mbar_wait(&full_bar[st], ph)) { ok = false; s_fail = 1; break; }
+    int kt = 0, pg = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      int pid, m0, n0;
+      if (!oz_tile(descs, tile_start, nprob, tile, pid, m0, n0)) continue;
+      const OzDesc& d = descs[pid];
+      const int wt = d.w / BK;
+      for (int p = 0; p < d.npass; ++p, ++pg) {
+        const int acc = pg % NACC, use = pg / NACC;
+        bool ok = !s_fail && mbar_wait(&acce_bar[acc], (use & 1) ^ 1);
+        if (!ok) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* sa = smem + st * STAGE_BYTES;
-        unsigned char* sb = sa + A_BYTES;
-        const uint64_t da = smem_desc(sa), db = smem_desc(sb);
+        const int nk = d.pnp[p] * wt;
+        for (int i = 0; i < nk && ok; ++i, ++kt) {
+          const int st = kt % STAGES;
+          const uint32_t ph = (kt / STAGES) & 1;
+          if (!mbar_wait(&full_bar[st], ph)) { ok = false; s_fail = 1; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* sa = smem + st * STAGE_BYTES;
+          unsigned char* sb = sa + A_BYTES;
+          const uint64_t da = smem_desc(sa), db = smem_desc(sb);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
-          mma_bf16(tmem + acc * BN, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, (i | k) != 0);
-        mma_commit(&empty_bar[st]);
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(tmem + acc * BN, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, (i | k) != 0);
+          mma_commit(&empty_bar[st]);
+        }
+        if (ok) mma_commit(&accf_bar[acc]);
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accf_bar[acc])) : "memory");
       }
-      if (ok) mma_commit(&accf_bar[acc]);
-      else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accf_bar[acc])) : "memory");
     }
   } else if (warp >= 2) {
-    // ---- epilogue: drain every pass into FP64 registers
+    // ---- epilogue: drain every pass of every tile into int64 fixed point
     // Every pass sum is an exact integer below 2^24.  They are added in
     // int64 fixed point with FIX = 37 fractional bits of the level-0 unit
     // (|total| < 2^24 * 1.1 * 2^37 < 2^62): levels with beta*d <= 37 are
     // exact, deeper ones round by at most half a unit of 2^-37, so FP64
     // arithmetic is needed only once per output element.
     const int q4 = warp & 3;
-    const int row = m0 + q4 * 32 + lane;
-    long long re[BN / 2], im[BN / 2];
+    int pg = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      int pid, m0, n0;
+      if (!oz_tile(descs, tile_start, nprob, tile, pid, m0, n0)) continue;
+      const OzDesc& d = descs[pid];
+      const int row = m0 + q4 * 32 + lane;
+      if (threadIdx.x - 64 < BN / 2) {
+        const int j = (n0 >> 1) + (threadIdx.x - 64);
+        colscale[threadIdx.x - 64] = (2 * j < d.n2) ? pow2(exp_of(d.mB[j])) : 0.0;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // epilogue warps only
+      long long re[BN / 2], im[BN / 2];
 #pragma unroll
-    for (int e = 0; e < BN / 2; ++e) { re[e] = 0; im[e] = 0; }
-    bool ok = true;
-    for (int p = 0; p < npass; ++p) {
-      const int acc = p % NACC, use = p / NACC;
-      if (ok && !mbar_wait(&accf_bar[acc], use & 1)) ok = false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int sh = 37 - d.beta_bits * d.pd[p];  // shift of this level into the fixed point
-      if (ok && !s_fail) {
+      for (int e = 0; e < BN / 2; ++e) { re[e] = 0; im[e] = 0; }
+      bool ok = true;
+      for (int p = 0; p < d.npass; ++p, ++pg) {
+        const int acc = pg % NACC, use = pg / NACC;
+        if (ok && !s_fail && !mbar_wait(&accf_bar[acc], use & 1)) { ok = false; s_fail = 1; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int sh = 37 - d.beta_bits * d.pd[p];  // shift of this level into the fixed point
+        if (ok && !s_fail) {
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t v[32];
-          const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + half * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (sh >= 0) {
+          for (int half = 0; half < 2; ++half) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + half * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (sh >= 0) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              re[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
-              im[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
-            }
-          } else {
-            const int rs = -sh;
-            const long long rnd = 1ll << (rs - 1);
+              for (int e = 0; e < 16; ++e) {
+                re[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
+                im[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
+              }
+            } else {
+              const int rs = -sh;
+              const long long rnd = 1ll << (rs - 1);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              re[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
-              im[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
+              for (int e = 0; e < 16; ++e) {
+                re[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
+                im[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
+              }
             }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[acc])) : "memory");
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[acc])) : "memory");
-    }
-    if (ok && !s_fail && row < d.m) {
-      // value = fixed / 2^37 * 2^{-2 beta} * 2^{eA[row]} * 2^{eB[j]}
-      const double rs_row = pow2(exp_of(d.mA[row]) - 37 - 2 * d.beta_bits);
-      const bool unit_alpha = d.alpha.y == 0.0 && (d.alpha.x == 1.0 || d.alpha.x == -1.0);
+      if (ok && !s_fail && row < d.m) {
+        // value = fixed / 2^37 * 2^{-2 beta} * 2^{eA[row]} * 2^{eB[j]}
+        const double rs_row = pow2(exp_of(d.mA[row]) - 37 - 2 * d.beta_bits);
+        const bool unit_alpha = d.alpha.y == 0.0 && (d.alpha.x == 1.0 || d.alpha.x == -1.0);
 #pragma unroll
-      for (int e = 0; e < BN / 2; ++e) {
-        const int j = (n0 >> 1) + e;
-        if (2 * j < d.n2) {
-          const double sc = rs_row * colscale[e];
-          z64 out = zmk((double)re[e] * sc, (double)im[e] * sc);
-          if (unit_alpha) { if (d.alpha.x < 0.0) { out.x = -out.x; out.y = -out.y; } }
-          else out = zmul(d.alpha, out);
-          if (d.cmode == 1) {
-            const size_t fi = (size_t)row * d.ldcf + j;
-            out = zadd(out, zmul(d.beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
-          } else if (d.cmode == 2) {
-            if (row == j) out = zadd(out, d.beta);
-          } else if (d.beta.x != 0.0 || d.beta.y != 0.0) {
-            out = zadd(out, zmul(d.beta, d.c[(size_t)row * d.ldc + j]));
+        for (int e = 0; e < BN / 2; ++e) {
+          const int j = (n0 >> 1) + e;
+          if (2 * j < d.n2) {
+            const double sc = rs_row * colscale[e];
+            z64 out = zmk((double)re[e] * sc, (double)im[e] * sc);
+            if (unit_alpha) { if (d.alpha.x < 0.0) { out.x = -out.x; out.y = -out.y; } }
+            else out = zmul(d.alpha, out);
+            if (d.cmode == 1) {
+              const size_t fi = (size_t)row * d.ldcf + j;
+              out = zadd(out, zmul(d.beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
+            } else if (d.cmode == 2) {
+              if (row == j) out = zadd(out, d.beta);
+            } else if (d.beta.x != 0.0 || d.beta.y != 0.0) {
+              out = zadd(out, zmul(d.beta, d.c[(size_t)row * d.ldc + j]));
+            }
+            d.c[(size_t)row * d.ldc + j] = out;
           }
-          d.c[(size_t)row * d.ldc + j] = out;
         }
       }
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // colscale is rewritten for the next tile
     }
   }
   __syncthreads();
@@ -447,7 +473,14 @@ cudaError_t launch_oz_gemm(const OzDesc* d, const int* tile_start, int nprob, in
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  oz_gemm_kernel<<<total, OZ_THREADS, oz_smem_bytes(), st>>>(d, tile_start, nprob, err);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 148;
+  }
+  const int grid = total < nsm ? total : nsm;  // persistent: one CTA per SM
+  oz_gemm_kernel<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(d, tile_start, nprob, total, err);
   return cudaGetLastError();
 }
 
