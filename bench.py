@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -230,6 +231,8 @@ def main():
         sel = [mine[(step * P + i) % len(mine)] for i in range(P)]
         return [e for e, _ in sel], [k for _, k in sel]
 
+    tune = {}
+
     def handle(prec, device_ptrs=1, profile=0):
         h = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=device_ptrs,
                       stream=stream.cuda_stream, precision=prec, profile=profile, use_graphs=0 if a.no_graphs else 1)
@@ -240,6 +243,9 @@ def main():
                 else:
                     h.set_device(k, d)
         stream.synchronize()
+        # LU panel width and update arithmetic for this s_b, measured once per
+        # precision and cached on disk for later handles
+        tune[prec] = h.autotune(a.s_b, 2 * P, os.path.join(tempfile.gettempdir(), "splitsolve_autotune.txt"))
         return h
 
     def step(hh, s, inj, want_x=True):
@@ -248,6 +254,7 @@ def main():
         xs, st1, _ = hh.solve(E, K, inj, want_x=want_x)
         T, err, st2, _ = hh.transmission(E, K)
         Tn = T.cpu().numpy() if hasattr(T, "cpu") else np.asarray(T)
+        hh.last_err = np.asarray(err.cpu().numpy() if hasattr(err, "cpu") else err)
         return it, Tn, np.maximum(np.maximum(st0, st1), st2)
 
     def measure(prec, steps, warmup, clocks=None, start=None):
@@ -260,7 +267,7 @@ def main():
                 step(h, s_, inj_dev)
         stream.synchronize()
         launches0 = h.launch_count()
-        iters, Ts, sts = [], [], []
+        iters, Ts, sts, errs = [], [], [], []
         barrier()
         torch.cuda.synchronize()
         ctx = clocks if clocks is not None else _Null()
@@ -271,6 +278,7 @@ def main():
             with torch.cuda.stream(stream):
                 for s_ in range(start, start + steps):
                     it, T, st = step(h, s_, inj_dev)
+                    errs.append(h.last_err)
                     iters.append(it)
                     Ts.append(T)
                     sts.append(st)
@@ -295,7 +303,8 @@ def main():
             kern[name] = {"ms": ms, "launches": n, "flops": fl, "issued": hp.profile_issued(name)}
         hp.close()
         return dict(t=t, value=P * steps * world / t, tflops=flops * world / t / 1e12, kern=kern, launches=launches,
-                    T=np.concatenate(Ts), ok=bool(np.all(np.concatenate(sts) == 0)), steps=steps)
+                    T=np.concatenate(Ts), ok=bool(np.all(np.concatenate(sts) == 0)), steps=steps,
+                    status=np.concatenate(sts), err=np.concatenate(errs))
 
     run_mixed = a.precision in ("mixed", "both")
     run_fp64 = a.precision in ("fp64", "both")
@@ -382,12 +391,18 @@ def main():
             "tflops": head["tflops"],
             "roofline": roofline,
             "kernels_ms": {k: round(v["ms"], 3) for k, v in kern.items()},
+            "kernels_launches": {k: v["launches"] for k, v in kern.items() if v["launches"]},
             "mixed_vs_fp64": cmp,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": head["launches"],
             "clocks": clk.summary(),
+            "lu_tune": {("fp64" if k == ss.SS_FP64 else "mixed"): {"panel_width": v[0], "outer_width": v[1],
+                                                                  "update": v[2], "ms": v[3]}
+                        for k, v in tune.items()},
             "status_ok": head["ok"],
+            "status_counts": {str(int(k)): int(v) for k, v in zip(*np.unique(head["status"], return_counts=True))},
+            "err_est_max": float(np.max(head["err"])),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -72,7 +72,7 @@ typedef struct {
   double eta;         /* lead broadening: z = E + i*eta inside the leads (default 1e-10) */
   double decim_tol;   /* doubling stops when max(|a|_1,|b|_1) <= decim_tol*|D|_1 (1e-14) */
   int decim_max_iter; /* doubling cap -> SS_ERR_NOT_CONVERGED (default 100)           */
-  double ir_tol;      /* mixed: refinement stops at ||r||/||Inj|| <= ir_tol (1e-14)    */
+  double ir_tol;      /* mixed: refinement target: backward error <= ir_tol (1e-14)   */
   int ir_max_iter;    /* mixed: refinement cap (default 10)                            */
   int warm_start;     /* reserved: 1 seeds the surface GF from a trained network       */
   void* stream;       /* cudaStream_t to enqueue on (NULL = legacy default stream)     */
@@ -122,15 +122,17 @@ int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id,
  * x: per point (n_b*s_b) x n_inj row-major; may be NULL, in which case only
  * the factors and G_1n are computed (and cached for ss_transmission).
  * 1 <= n_inj <= cfg.max_inj.  In the mixed modes x is refined in FP64 until
- * ||Inj - (A - Sigma) x|| <= ir_tol ||Inj|| (status SS_ERR_NOT_CONVERGED at
- * the cap).  The transmission of each point is computed on the way and kept
+ * the normwise backward error ||Inj - (A - Sigma) x||_F /
+ * (||A - Sigma||_F ||x||_F + ||Inj||_F) is <= ir_tol, until a correction no
+ * longer halves the worst one of the batch, or until ir_max_iter
+ * corrections; a point left above ir_tol gets SS_ERR_NOT_CONVERGED.  The transmission of each point is computed on the way and kept
  * for ss_transmission. */
 int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id,
              int n_inj, const ss_c64* inj, ss_c64* x, int* status);
 
 /* Transmission T(E,k) = Re Tr[Gamma_L G_1n Gamma_R G_1n^H] per point (T:
  * n_pts doubles).  err_est (optional): FP64 path: |Im Tr| / max(1,|T|);
- * mixed path: the relative FP64 residual of the refined solve.  Reuses the
+ * mixed path: the normwise backward error of the refined x (see ss_solve).  Reuses the
  * cached results of an immediately preceding ss_solve / ss_self_energy on the
  * same points; otherwise runs the whole pipeline. */
 int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id,
@@ -193,11 +195,17 @@ const char* ss_noalloc_last_error(void);
  * solve of blocks of size s_b: times a synthetic batch of n_problems
  * systems [D | B] (s_b x 2 s_b) for each panel width (8 and 16, or 32 above
  * s_b = 512) and, in SS_MIXED_OZAKI, each update arithmetic (0: FP64 SIMT,
- * 2: exact tensor-core products), and keeps the fastest for this handle.
+ * 2: exact tensor-core products) with one-level blocking or two-level
+ * blocking of outer width 64, 128 or 256 (below s_b), and keeps the fastest
+ * for this handle.  The factorisation is the block LU of Sec. 3B; the choice
+ * changes the order of FP64 roundings only.
  * cache_path (optional): a text file of lines "precision s_b n_problems nb
- * upd ms"; a matching line is reused without timing, a new result is appended.
- * Outputs (optional, host): chosen nb, upd, and its time in ms. */
-int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb, int* upd, double* ms);
+ * nbo upd ms"; a matching line is reused without timing, a new result is
+ * appended.
+ * Outputs (optional, host): chosen panel width nb, outer width nbo (0: one
+ * level), update arithmetic upd, and its time in ms. */
+int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb, int* nbo, int* upd,
+                double* ms);
 
 /* ------------------------------------------------------------------------
  * Learned warm start of the surface Green's function (not in the paper).

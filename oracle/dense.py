@@ -116,6 +116,14 @@ def residual(M, x, b):
     return float(np.linalg.norm(M @ x - b) / np.linalg.norm(b))
 
 
+def backward_error(M, x, b):
+    """Normwise backward error in Frobenius norms (Rigal and Gaches):
+    ||M x - b|| / (||M|| ||x|| + ||b||), the smallest eps for which
+    (M + dM) x = b + db with ||dM|| <= eps ||M|| and ||db|| <= eps ||b||."""
+    r = M @ x - b
+    return float(np.linalg.norm(r) / (np.linalg.norm(M) * np.linalg.norm(x) + np.linalg.norm(b)))
+
+
 def rel_T_err(T, T_ref):
     """|T - T_ref| / max(1, |T_ref|): a relative error that stays defined in gaps."""
     return abs(T - T_ref) / max(1.0, abs(T_ref))

@@ -102,7 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.ss_mlp_last_error.argtypes = [vp]
     lib.ss_mlp_last_error.restype = C.c_char_p
     lib.ss_set_warm_start.argtypes = [vp, vp, C.c_int, C.c_double]
-    lib.ss_autotune.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, ip, ip, dp]
+    lib.ss_autotune.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, ip, ip, ip, dp]
     lib.ss_autotune.restype = C.c_int
     lib.ss_surface_gf.argtypes = [vp, C.c_int, dp, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double, vp, ip, ip, ip]
     for name in ("ss_mlp_create", "ss_mlp_destroy", "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward",
@@ -298,12 +298,12 @@ class Handle:
         return out, st, rc
 
     def autotune(self, s_b, n_problems, cache_path=None):
-        """ss_autotune: returns (panel width, update arithmetic, ms)."""
-        nb, upd, ms = C.c_int(), C.c_int(), C.c_double()
+        """ss_autotune: returns (panel width, outer width (0: one level), update arithmetic, ms)."""
+        nb, nbo, upd, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
         cp = None if cache_path is None else str(cache_path).encode()
-        self._check(self._lib.ss_autotune(self._h, int(s_b), int(n_problems), cp, C.byref(nb), C.byref(upd),
-                                          C.byref(ms)))
-        return nb.value, upd.value, ms.value
+        self._check(self._lib.ss_autotune(self._h, int(s_b), int(n_problems), cp, C.byref(nb), C.byref(nbo),
+                                          C.byref(upd), C.byref(ms)))
+        return nb.value, nbo.value, upd.value, ms.value
 
     def set_warm_start(self, net, side, out_scale):
         """ss_set_warm_start: attach a trained MLP to lead `side` (0 left, 1 right)."""

@@ -36,6 +36,9 @@ using namespace ss;
 namespace {
 
 constexpr int LU_NB = 0;  // panel width chosen per group from its largest block
+// Outer block width of the two-level LU in the mixed path: the exact
+// tensor-core trailing updates then have depth 128 instead of the panel width.
+inline int lu_outer_default(int smax) { return smax >= 256 ? 128 : (smax >= 128 ? 64 : 0); }
 constexpr int MAX_K_ID = 4096;
 
 std::string g_create_error;
@@ -207,9 +210,9 @@ struct ss_handle {
   Plan p_warm_iter, p_warm_judge, p_final_g;
   Plan p_ir_res, p_ir_cor;
   // autotuned LU settings per block size: panel width and update arithmetic
-  struct Tune { int nb; int upd; double ms; };
+  struct Tune { int nb; int nbo; int upd; double ms; };
   std::map<int, Tune> tune;
-  std::vector<double> c_err;  // relative FP64 residual of the last refined solve
+  std::vector<double> c_err;  // normwise backward error of the last refined solve
   Prof* P() { return cfg.profile ? &prof : nullptr; }
   // cache of the last chunk
   std::vector<double> cE;
@@ -250,11 +253,11 @@ bool big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
 void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
   int smax = 0;
   for (auto& d : ds) smax = std::max(smax, d.s);
-  int nb = LU_NB;
+  int nb = LU_NB, nbo = h->mixed() ? lu_outer_default(smax) : 0;
   Plan::Updates upd = h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64;
   auto it = h->tune.find(smax);
-  if (it != h->tune.end()) { nb = it->second.nb; upd = (Plan::Updates)it->second.upd; }
-  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err)) h->plan_error = true;
+  if (it != h->tune.end()) { nb = it->second.nb; nbo = it->second.nbo; upd = (Plan::Updates)it->second.upd; }
+  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo)) h->plan_error = true;
 }
 
 // ---------------------------------------------------------- self-energies
@@ -550,11 +553,12 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
 
 // ------------------------------------------------------------ refinement
 // Residual r = Inj - (A - Sigma) x in FP64 for every block, and ||r||_F^2.
-void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr, double* bb) {
+void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr, double* xx) {
   Plan& R = h->p_ir_res;
   R.clear();
   const int P = (int)pts.size();
   R.memset0(rr, sizeof(double) * P);
+  R.memset0(xx, sizeof(double) * P);
   std::vector<FormDesc> f;
   std::vector<GemmDesc> gd, gu, gl, gs1, gs2;
   std::vector<Norm1Desc> nr;
@@ -584,6 +588,7 @@ void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr,
     gs2.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.x + (n - 1) * bs, ninj), w.r + (n - 1) * bs, ninj, ONE,
                         ONE));
     nr.push_back({w.r, ninj, n * s, ninj, rr + p, nullptr});
+    nr.push_back({w.x, ninj, n * s, ninj, xx + p, nullptr});
   }
   R.form(f);
   R.gemm(gd);
@@ -592,12 +597,45 @@ void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr,
   R.gemm(gs1);
   R.gemm(gs2);
   R.frob2(nr);
-  (void)bb;
+}
+
+// ||A - Sigma||_F^2 of every point (block tridiagonal: diagonal blocks with
+// the self-energies on the first and last one, the upper blocks counted
+// twice for their conjugate-transposed lower partners) and ||Inj||_F^2.
+void build_ir_norms(Plan& N, std::vector<PW>& pts, int ninj, double* mm, double* bb) {
+  const int P = (int)pts.size();
+  N.memset0(mm, sizeof(double) * P);
+  N.memset0(bb, sizeof(double) * P);
+  std::vector<FormDesc> f;
+  std::vector<Norm1Desc> nb_d;
+  for (int p = 0; p < P; ++p) {
+    const PW& w = pts[p];
+    const int n = w.n, s = w.s;
+    const size_t ss2 = (size_t)s * s;
+    const KData* kd = w.kd;
+    const z64 E = make_double2(w.E, 0.0);
+    for (int i = 1; i <= n; ++i) {
+      FormDesc d = fformed(nullptr, 0, kd->Sd + (i - 1) * ss2, kd->Hd + (i - 1) * ss2, E, s, s, s);
+      if (i == 1) { d.z = w.sig[0]; d.ldz = s; d.az = MONE; }
+      if (i == n) { d.v = w.sig[1]; d.ldv = s; d.av = MONE; }
+      d.nrm = mm + p; d.nw = 1.0;
+      f.push_back(d);
+      if (i < n) {
+        FormDesc u = fformed(nullptr, 0, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s);
+        u.nrm = mm + p; u.nw = 2.0;
+        f.push_back(u);
+      }
+    }
+    nb_d.push_back({w.inj, ninj, 2 * s, ninj, bb + p, nullptr});
+  }
+  N.form(f);
+  N.frob2(nb_d);
 }
 
 // Correction delta = M~^-1 r with the stored D_i^-1 (block UL substitution of
 // the first-column sweep) and R^-1 (Sherman-Morrison-Woodbury), then x += delta.
-// The correction only has to be approximate, so its products use FP32 arithmetic.
+// FP64 products: with FP32 ones the correction stops contracting on long
+// devices (its error times the condition number of A - Sigma nears 1).
 void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax) {
   Plan& C = h->p_ir_cor;
   C.clear();
@@ -624,8 +662,8 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
       }
     }
     C.form(f);
-    C.gemm(g1, true);
-    C.gemm(g2, true);
+    C.gemm(g1);
+    C.gemm(g2);
   }
   // forward: y_1 = w_1 ; y_i = w_i - Di^-1 (U_{i-1}^H y_{i-1})  (in place in w)
   for (int t = 1; t < nmax; ++t) {
@@ -641,8 +679,8 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
                          plain(wi - bs, ninj), w.tv, ninj, ONE, ZERO));
       g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, MONE, ONE));
     }
-    C.gemm(g1, true);
-    C.gemm(g2, true);
+    C.gemm(g1);
+    C.gemm(g2);
   }
   // SMW: z' = R^-1 [Sigma_L y_1 ; Sigma_R y_n] ; x_i += y_i + Q_i z'_top + P_i z'_bot
   std::vector<GemmDesc> gz1, gz2, gr, gx1, gx2;
@@ -663,12 +701,12 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
       gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.tv + bs, ninj), xi, ninj, ONE, ONE));
     }
   }
-  C.gemm(gz1, true);
-  C.gemm(gz2, true);
-  C.gemm(gr, true);
+  C.gemm(gz1);
+  C.gemm(gz2);
+  C.gemm(gr);
   C.form(fx);
-  C.gemm(gx1, true);
-  C.gemm(gx2, true);
+  C.gemm(gx1);
+  C.gemm(gx2);
   (void)P;
 }
 
@@ -775,7 +813,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     for (auto& w : pts) { carve_point(c, w, h->cfg.max_inj, h->mixed()); nmax = std::max(nmax, w.n); }
     // device scalars: act, iters, conv (2P each), decim info (4P), sweep info (2P*nmax), bound info (P)
     const size_t ni = 2 * P * 3 + 4 * P + 2 * (size_t)P * nmax + P;
-    int rc = ensure_scalars(h, ni, 3 * 2 * P + 2 * P, P);
+    int rc = ensure_scalars(h, ni, 3 * 2 * P + 4 * P, P);
     if (rc) return rc;
     int* act = h->dint;
     int* itr = act + 2 * P;
@@ -786,8 +824,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     double* na = h->ddbl;
     double* nb = na + 2 * P;
     double* nd = nb + 2 * P;
-    double* rr = nd + 2 * P;  // refinement: ||r||^2 and ||Inj||^2 per point
+    double* rr = nd + 2 * P;  // refinement: ||r||^2, ||Inj||^2, ||A - Sigma||^2, ||x||^2 per point
     double* bb = rr + P;
+    double* mm = bb + P;
+    double* xx = mm + P;
 
     // inputs
     if (want.solve && want.ninj > 0) {
@@ -880,32 +920,37 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
       CK(h->p_bound.run(st, &h->nlaunch, h->P()), "boundary");
       if (h->mixed() && want.x && want.ninj > 0) {
-        // FP64 iterative refinement of x until ||r|| <= ir_tol ||Inj|| or the cap
-        build_ir_residual(h, pts, want.ninj, rr, bb);
+        // FP64 iterative refinement of x until the normwise backward error
+        // ||r|| / (||A - Sigma|| ||x|| + ||Inj||) (Frobenius norms) is <= ir_tol
+        build_ir_residual(h, pts, want.ninj, rr, xx);
         build_ir_correction(h, pts, want.ninj, nmax);
         Plan nrm;
-        std::vector<Norm1Desc> nb_d;
-        for (int p = 0; p < P; ++p) nb_d.push_back({pts[p].inj, want.ninj, 2 * pts[p].s, want.ninj, bb + p, nullptr});
-        nrm.memset0(bb, sizeof(double) * P);
-        nrm.frob2(nb_d);
+        build_ir_norms(nrm, pts, want.ninj, mm, bb);
         CK(nrm.upload(st), "upload");
-        CK(nrm.run(st, &h->nlaunch, h->P()), "||Inj||");
+        CK(nrm.run(st, &h->nlaunch, h->P()), "||A - Sigma||, ||Inj||");
         CK(h->p_ir_res.upload(st), "upload");
         CK(h->p_ir_cor.upload(st), "upload");
-        std::vector<double> hr(P), hb(P);
+        std::vector<double> hr(P), hb(P), hm(P), hx(P);
         CK(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
+        CK(cudaMemcpyAsync(hm.data(), mm, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
+        double prev = HUGE_VAL;
         for (int it = 0;; ++it) {
           CK(h->p_ir_res.run(st, &h->nlaunch, h->P()), "residual");
           CK(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
+          CK(cudaMemcpyAsync(hx.data(), xx, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
           CK(cudaStreamSynchronize(st), "refinement sync");
           double worst_rel = 0.0;
           for (int p = 0; p < P; ++p) {
-            const double rel = std::sqrt(hr[p] / std::max(hb[p], 1e-300));
+            const double den = std::sqrt(hm[p]) * std::sqrt(hx[p]) + std::sqrt(hb[p]);
+            const double rel = std::sqrt(hr[p]) / std::max(den, 1e-300);
             ir_err[p] = rel;
             worst_rel = std::max(worst_rel, std::isfinite(rel) ? rel : 1e300);
           }
           ir_steps = it;
-          if (worst_rel <= h->cfg.ir_tol || it >= h->cfg.ir_max_iter) break;
+          // stop at the tolerance, at the cap, or when a correction no longer
+          // halves the residual (FP64 working accuracy: more steps cannot help)
+          if (worst_rel <= h->cfg.ir_tol || it >= h->cfg.ir_max_iter || worst_rel > 0.5 * prev) break;
+          prev = worst_rel;
           CK(h->p_ir_cor.run(st, &h->nlaunch, h->P()), "correction");
         }
       }
@@ -1226,27 +1271,28 @@ int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, d
   return rc;
 }
 
-int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb_out, int* upd_out,
-                double* ms_out) {
+int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb_out, int* nbo_out,
+                int* upd_out, double* ms_out) {
   if (!h) return SS_ERR_ARG;
   h->err.clear();
   if (s_b < 1 || s_b > h->cfg.s_b_max || n_problems < 1) return fail(h, SS_ERR_ARG, "ss_autotune: bad sizes");
   const int prec = h->cfg.precision;
   auto report = [&](const ss_handle::Tune& t) {
     if (nb_out) *nb_out = t.nb;
+    if (nbo_out) *nbo_out = t.nbo;
     if (upd_out) *upd_out = t.upd;
     if (ms_out) *ms_out = t.ms;
     return SS_OK;
   };
-  // cache lines: "<precision> <s_b> <n_problems> <nb> <upd> <ms>"
+  // cache lines: "<precision> <s_b> <n_problems> <nb> <nbo> <upd> <ms>"
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
-      int pr, sb, np, nb, upd;
+      int pr, sb, np, nb, nbo, upd;
       double ms;
       bool hit = false;
       ss_handle::Tune t{};
-      while (std::fscanf(f, "%d %d %d %d %d %lf", &pr, &sb, &np, &nb, &upd, &ms) == 6)
-        if (pr == prec && sb == s_b && np == n_problems) { t = {nb, upd, ms}; hit = true; }
+      while (std::fscanf(f, "%d %d %d %d %d %d %lf", &pr, &sb, &np, &nb, &nbo, &upd, &ms) == 7)
+        if (pr == prec && sb == s_b && np == n_problems) { t = {nb, nbo, upd, ms}; hit = true; }
       std::fclose(f);
       if (hit) { h->tune[s_b] = t; return report(t); }
     }
@@ -1280,10 +1326,14 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   std::vector<ss_handle::Tune> cands;
   const int nbs[2] = {8, s_b <= 512 ? 16 : 32};
   for (int nb : nbs) {
-    cands.push_back({nb, (int)Plan::UPD_FP64, 0.0});
-    if (h->mixed()) cands.push_back({nb, (int)Plan::UPD_EXACT_TC, 0.0});
+    cands.push_back({nb, 0, (int)Plan::UPD_FP64, 0.0});
+    if (h->mixed()) {
+      cands.push_back({nb, 0, (int)Plan::UPD_EXACT_TC, 0.0});
+      for (int nbo : {64, 128, 256})
+        if (nbo < s_b) cands.push_back({nb, nbo, (int)Plan::UPD_EXACT_TC, 0.0});
+    }
   }
-  ss_handle::Tune best{-1, 0, 0.0};
+  ss_handle::Tune best{-1, 0, 0, 0.0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1296,7 +1346,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
       ds.push_back(L);
     }
     Plan P;
-    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err)) continue;
+    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err, c.nbo)) continue;
     e = P.upload(st);
     float best_ms = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
@@ -1320,7 +1370,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   h->tune[s_b] = best;
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
-      std::fprintf(f, "%d %d %d %d %d %.6f\n", prec, s_b, n_problems, best.nb, best.upd, best.ms);
+      std::fprintf(f, "%d %d %d %d %d %d %.6f\n", prec, s_b, n_problems, best.nb, best.nbo, best.upd, best.ms);
       std::fclose(f);
     }
   }

@@ -76,6 +76,9 @@ struct FormDesc {
   const z64* z; int ldz; int tz; z64 az;
   z64 gamma;
   const int* active;
+  const z64* v; int ldv; z64 av;  // fourth term (not transposed)
+  // norm mode (nrm != nullptr): nothing is written; *nrm += nw * sum |value|^2
+  double* nrm; double nw;
 };
 
 // Blocked LU with partial pivoting of the leading s x s block of the
@@ -124,7 +127,10 @@ int zform_tiles(int rows, int cols);
 // register-resident panel kernel within 32 complex values per thread).
 int lu_panel_width(int smax);
 void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st);
-void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int max_cols,
+// nbo > 0: two-level blocking with outer width nbo (the solve stops at the
+// outer block's end); far != 0: solve the columns right of the outer block
+// without swaps.
+void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int far, int max_cols,
                         cudaStream_t st);
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs,
                             cudaStream_t st);

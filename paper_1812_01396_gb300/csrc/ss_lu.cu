@@ -12,6 +12,11 @@
 //   lu_rowblock applies the panel's row swaps to every other column and
 //               forms U12 = L11^-1 A12 (and L11^-1 B1) in place;
 //   (zgemm)     A22 -= L21 U12 over the trailing columns, RHS included.
+// Two-level blocking (outer width nbo, a multiple of nb) keeps the nb-wide
+// steps inside the outer block and defers the columns right of it: after the
+// block, its rows are solved there panel by panel (lu_rowblock `far` plus
+// FP64 updates inside the block) and the trailing matrix gets one update of
+// depth nbo, which is what the exact tensor-core GEMM wants.
 // After the last panel, B holds L^-1 P B; per panel from the bottom:
 //   lu_backsub_diag  B_k = U_kk^-1 B_k,  (zgemm) B_0..k -= U_0..k,k B_k.
 //
@@ -245,14 +250,19 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) lu_panel_reg_kernel(const Lu
 constexpr int RB_THREADS = 128;
 
 // Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
-// columns to its right (right-hand sides included).
+// columns to its right (right-hand sides included).  With an outer block
+// width nbo > 0 (two-level blocking) the solve stops at the end of the outer
+// block, K1 = min(K0 + nbo, s): columns from K1 on are swapped now and solved
+// later by the `far` variant, which applies no swaps and solves the rows of
+// this panel on columns K1..ncols-1 only.
 __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* __restrict__ descs,
-                                                                 int k0, int nb) {
+                                                                 int k0, int nb, int nbo, int far) {
   const LuDesc d = descs[blockIdx.y];
   if (d.active && __ldg(d.active) == 0) return;
   const int s = d.s;
   if (k0 >= s) return;
   const int nbw = min(nb, s - k0);
+  const int K1 = nbo > 0 ? min((k0 / nbo) * nbo + nbo, s) : d.ncols;
   __shared__ z64 Ls[MAXNB][MAXNB + 1];
   __shared__ int piv[MAXNB];
   for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
@@ -262,22 +272,28 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
   if (threadIdx.x < nbw) piv[threadIdx.x] = d.ipiv[k0 + threadIdx.x];
   __syncthreads();
   const int q = blockIdx.x * RB_THREADS + threadIdx.x;
-  const int nout = d.ncols - nbw;
-  if (q >= nout) return;
-  const int c = (q < k0) ? q : q + nbw;
   z64* __restrict__ w = d.w;
   const size_t ld = d.ldw;
-  for (int j = 0; j < nbw; ++j) {
-    const int p = piv[j];
-    if (p != k0 + j) {
-      z64* a = w + (size_t)(k0 + j) * ld + c;
-      z64* b = w + (size_t)p * ld + c;
-      const z64 t = *a;
-      *a = *b;
-      *b = t;
+  int c;
+  if (far) {
+    if (q >= d.ncols - K1) return;
+    c = K1 + q;
+  } else {
+    const int nout = d.ncols - nbw;
+    if (q >= nout) return;
+    c = (q < k0) ? q : q + nbw;
+    for (int j = 0; j < nbw; ++j) {
+      const int p = piv[j];
+      if (p != k0 + j) {
+        z64* a = w + (size_t)(k0 + j) * ld + c;
+        z64* b = w + (size_t)p * ld + c;
+        const z64 t = *a;
+        *a = *b;
+        *b = t;
+      }
     }
+    if (c < k0 || c >= K1) return;
   }
-  if (c < k0) return;
   z64 x[MAXNB];
 #pragma unroll
   for (int j = 0; j < MAXNB; ++j)
@@ -367,10 +383,11 @@ void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaS
   else lu_panel_kernel<<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
 }
 
-void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int max_cols, cudaStream_t st) {
+void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int far, int max_cols,
+                        cudaStream_t st) {
   if (nprob <= 0 || max_cols <= 0) return;
   dim3 grid((max_cols + RB_THREADS - 1) / RB_THREADS, nprob);
-  lu_rowblock_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+  lu_rowblock_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
 }
 
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs, cudaStream_t st) {

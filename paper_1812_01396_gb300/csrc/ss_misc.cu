@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(FNT) zform_kernel(const FormDesc* __restrict__
   const int t = blockIdx.x - __ldg(tile_start + pid);
   const int r0 = (t / tiles_c) * FT, c0 = (t % tiles_c) * FT;
   // each thread handles 4 elements of the 32 x 32 tile
+  double sq = 0.0;
   for (int e = threadIdx.x; e < FT * FT; e += FNT) {
     const int r = r0 + e / FT, c = c0 + e % FT;
     if (r >= d.rows || c >= d.cols) continue;
@@ -43,7 +44,21 @@ __global__ void __launch_bounds__(FNT) zform_kernel(const FormDesc* __restrict__
     if (d.x) v = zadd(v, zmul(d.ax, opget(d.x, d.ldx, d.tx, r, c)));
     if (d.y) v = zadd(v, zmul(d.ay, opget(d.y, d.ldy, d.ty, r, c)));
     if (d.z) v = zadd(v, zmul(d.az, opget(d.z, d.ldz, d.tz, r, c)));
-    d.out[(size_t)r * d.ldo + c] = v;
+    if (d.v) v = zadd(v, zmul(d.av, d.v[(size_t)r * d.ldv + c]));
+    if (d.nrm) sq = fma(v.x, v.x, fma(v.y, v.y, sq));
+    else d.out[(size_t)r * d.ldo + c] = v;
+  }
+  if (d.nrm) {  // uniform per CTA
+    __shared__ double red[FNT / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int q = 0; q < FNT / 32; ++q) b += red[q];
+      atomicAdd(d.nrm, d.nw * b);
+    }
   }
 }
 

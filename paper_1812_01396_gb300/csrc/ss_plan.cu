@@ -238,7 +238,8 @@ bool Plan::tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pac
   return true;
 }
 
-bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err) {
+bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err,
+                    int nbo) {
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
@@ -250,34 +251,92 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   int smax = 0;
   for (auto& d : ds) smax = std::max(smax, d.s);
   if (nb <= 0) nb = lu_panel_width(smax);
-  // forward: panels left to right
-  for (int k0 = 0; k0 < smax; k0 += nb) {
+  if (nbo > 0 && (nbo <= nb || nbo % nb != 0)) nbo = 0;
+  // C -= A B with A at (ar, ac), B at (br, bc), C at (cr, cc) of the problem's W
+  auto upd_desc = [](const LuDesc& d, int m, int n, int k, int ar, int ac, int br, int bc, int cr, int cc) {
+    GemmDesc q{};
+    q.m = m; q.n = n; q.k = k;
+    q.a.p = d.w + (size_t)ar * d.ldw + ac; q.a.ld = d.ldw;
+    q.b.p = d.w + (size_t)br * d.ldw + bc; q.b.ld = d.ldw;
+    q.c = d.w + (size_t)cr * d.ldw + cc; q.ldc = d.ldw;
+    q.alpha = make_double2(-1.0, 0.0); q.beta = make_double2(1.0, 0.0);
+    q.active = d.active;
+    return q;
+  };
+  auto rowblock = [&](int k0, int far, int maxc) {
+    LaunchRec rr;
+    rr.kind = K_LU_ROW;
+    rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.nbo = nbo; rr.ival = far; rr.maxc = maxc;
+    recs_.push_back(rr);
+  };
+  auto panel = [&](int k0) {
     LaunchRec r;
     r.kind = K_LU_PANEL;
     r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = smax;
     recs_.push_back(r);
-    int maxc = 0;
-    std::vector<GemmDesc> g;
-    for (auto& d : ds) {
-      if (k0 >= d.s) continue;
-      const int nbw = std::min(nb, d.s - k0);
-      maxc = std::max(maxc, d.ncols - nbw);
-      const int m = d.s - k0 - nbw, n = d.ncols - k0 - nbw;
-      if (m <= 0 || n <= 0) continue;
-      GemmDesc q{};
-      q.m = m; q.n = n; q.k = nbw;
-      q.a.p = d.w + (size_t)(k0 + nbw) * d.ldw + k0; q.a.ld = d.ldw;
-      q.b.p = d.w + (size_t)k0 * d.ldw + k0 + nbw; q.b.ld = d.ldw;
-      q.c = d.w + (size_t)(k0 + nbw) * d.ldw + k0 + nbw; q.ldc = d.ldw;
-      q.alpha = make_double2(-1.0, 0.0); q.beta = make_double2(1.0, 0.0);
-      q.active = d.active;
-      g.push_back(q);
+  };
+  if (nbo <= 0) {
+    // forward: panels left to right
+    for (int k0 = 0; k0 < smax; k0 += nb) {
+      panel(k0);
+      int maxc = 0;
+      std::vector<GemmDesc> g;
+      for (auto& d : ds) {
+        if (k0 >= d.s) continue;
+        const int nbw = std::min(nb, d.s - k0);
+        maxc = std::max(maxc, d.ncols - nbw);
+        const int m = d.s - k0 - nbw, n = d.ncols - k0 - nbw;
+        if (m <= 0 || n <= 0) continue;
+        g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, k0 + nbw, k0 + nbw, k0 + nbw));
+      }
+      rowblock(k0, 0, maxc);
+      update(g);
     }
-    LaunchRec rr;
-    rr.kind = K_LU_ROW;
-    rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.maxc = maxc;
-    recs_.push_back(rr);
-    update(g);
+  } else {
+    for (int K0 = 0; K0 < smax; K0 += nbo) {
+      const int kend = std::min(K0 + nbo, smax);
+      // nb-wide steps inside the outer block
+      for (int k0 = K0; k0 < kend; k0 += nb) {
+        panel(k0);
+        int maxc = 0;
+        std::vector<GemmDesc> g;
+        for (auto& d : ds) {
+          if (k0 >= d.s) continue;
+          const int nbw = std::min(nb, d.s - k0), K1 = std::min(K0 + nbo, d.s);
+          maxc = std::max(maxc, d.ncols - nbw);
+          const int m = d.s - k0 - nbw, n = K1 - k0 - nbw;
+          if (m <= 0 || n <= 0) continue;
+          g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, k0 + nbw, k0 + nbw, k0 + nbw));
+        }
+        rowblock(k0, 0, maxc);
+        gemm(g, false, true);
+      }
+      // the block's rows on the columns right of it
+      for (int k0 = K0; k0 < kend; k0 += nb) {
+        int maxc = 0;
+        std::vector<GemmDesc> g;
+        for (auto& d : ds) {
+          if (k0 >= d.s) continue;
+          const int nbw = std::min(nb, d.s - k0), K1 = std::min(K0 + nbo, d.s);
+          maxc = std::max(maxc, d.ncols - K1);
+          const int m = K1 - k0 - nbw, n = d.ncols - K1;
+          if (m <= 0 || n <= 0) continue;
+          g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, K1, k0 + nbw, K1));
+        }
+        rowblock(k0, 1, maxc);
+        gemm(g, false, true);
+      }
+      // one trailing update of depth nbo
+      std::vector<GemmDesc> g;
+      for (auto& d : ds) {
+        if (K0 >= d.s) continue;
+        const int K1 = std::min(K0 + nbo, d.s);
+        const int m = d.s - K1, n = d.ncols - K1;
+        if (m <= 0 || n <= 0) continue;
+        g.push_back(upd_desc(d, m, n, K1 - K0, K1, K0, K0, K1, K1, K1));
+      }
+      update(g);
+    }
   }
   // backward substitution on the right-hand sides: panels right to left
   int maxrhs = 0;
@@ -291,19 +350,33 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
     recs_.push_back(r);
     if (k0 == 0) break;
     std::vector<GemmDesc> g;
-    for (auto& d : ds) {
-      if (k0 >= d.s || d.ncols <= d.s) continue;
-      const int nbw = std::min(nb, d.s - k0);
-      GemmDesc q{};
-      q.m = k0; q.n = d.ncols - d.s; q.k = nbw;
-      q.a.p = d.w + k0; q.a.ld = d.ldw;
-      q.b.p = d.w + (size_t)k0 * d.ldw + d.s; q.b.ld = d.ldw;
-      q.c = d.w + d.s; q.ldc = d.ldw;
-      q.alpha = make_double2(-1.0, 0.0); q.beta = make_double2(1.0, 0.0);
-      q.active = d.active;
-      g.push_back(q);
+    if (nbo <= 0) {
+      for (auto& d : ds) {
+        if (k0 >= d.s || d.ncols <= d.s) continue;
+        const int nbw = std::min(nb, d.s - k0);
+        g.push_back(upd_desc(d, k0, d.ncols - d.s, nbw, 0, k0, k0, d.s, 0, d.s));
+      }
+      update(g);
+      continue;
     }
-    update(g);
+    const int K0 = (k0 / nbo) * nbo;
+    if (k0 > K0) {
+      // rows of the outer block above this panel, FP64
+      for (auto& d : ds) {
+        if (k0 >= d.s || d.ncols <= d.s) continue;
+        const int nbw = std::min(nb, d.s - k0);
+        g.push_back(upd_desc(d, k0 - K0, d.ncols - d.s, nbw, K0, k0, k0, d.s, K0, d.s));
+      }
+      gemm(g, false, true);
+    } else {
+      // every row above the outer block, depth nbo
+      for (auto& d : ds) {
+        if (K0 >= d.s || d.ncols <= d.s) continue;
+        const int K1 = std::min(K0 + nbo, d.s);
+        g.push_back(upd_desc(d, K0, d.ncols - d.s, K1 - K0, 0, K0, K0, d.s, 0, d.s));
+      }
+      update(g);
+    }
   }
   return ok;
 }
@@ -410,7 +483,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_LU_ROW:
-        if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; }
+        if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.nbo, r.ival, r.maxc, st); ++n; }
         break;
       case K_LU_BACK: launch_lu_backsub_diag((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_FROB2: launch_frob2((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;

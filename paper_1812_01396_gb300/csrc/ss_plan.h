@@ -22,7 +22,7 @@ struct LaunchRec {
   LaunchKind kind;
   size_t off = 0, toff = 0;  // descriptor / tile-table offsets in the plan buffer
   int nprob = 0, tiles = 0;
-  int k0 = 0, nb = 0, maxc = 0;
+  int k0 = 0, nb = 0, maxc = 0, nbo = 0;
   double tol = 0.0;
   int cap = 0, count = 0, ival = 0;
   void* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -126,8 +126,11 @@ class Plan {
   // (panels, pivots and triangular blocks always stay FP64).
   enum Updates { UPD_FP64 = 0, UPD_FP32 = 1, UPD_EXACT_TC = 2 };
   // UPD_EXACT_TC slices the update operands into `pack` (cap bytes).
+  // nbo > nb (a multiple of nb): two-level blocking; only the depth-nbo
+  // trailing and back-substitution updates use `upd`, the nb-deep updates
+  // inside an outer block are FP64.
   bool lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
-                size_t cap = 0, int* err = nullptr);
+                size_t cap = 0, int* err = nullptr, int nbo = 0);
   void norm1(const std::vector<Norm1Desc>& ds) {
     if (ds.empty()) return;
     LaunchRec r;

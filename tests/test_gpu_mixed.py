@@ -63,7 +63,8 @@ def test_low_precision_modes_rejected_by_pipeline(ss):
 
 
 def test_refinement_residual_reported_and_small(ss):
-    """Mixed ss_solve refines x in FP64; ss_transmission reports the residual."""
+    """Mixed ss_solve refines x in FP64; ss_transmission reports its normwise
+    backward error."""
     dev = synth.make_device(6, 96, seed=44)[0]
     Es = [0.25, -0.5]
     inj = [synth.make_injection(96, 4, seed=i)[0] for i in range(2)]
@@ -80,8 +81,11 @@ def test_refinement_residual_reported_and_small(ss):
         # self-energies (the oracle's differ by the doubling's conditioning)
         M = dense.system_matrix(dev, Es[p], sL[p], sR[p])
         b = dense.full_injection(inj[p], dev.n_b, dev.s_b)
-        res = dense.residual(M, xs[p], b)
-        assert res < 1e-12, res
-        assert 0.0 <= err[p] < 1e-12
-        assert abs(err[p] - res) < 1e-13 + 0.5 * res
+        eta = dense.backward_error(M, xs[p], b)
+        assert eta < 1e-14, eta
+        assert 0.0 <= err[p] <= 1e-14
+        # the reported estimate carries the rounding of its own FP64 residual
+        # (about u sqrt(3 s_b) relative to ||A - Sigma|| ||x||)
+        assert abs(err[p] - eta) < 1e-14
+        assert dense.residual(M, xs[p], b) < 1e-11
         check_point({"sL": sL, "sR": sR, "T": T, "x": xs}, p, dev, Es[p], inj[p])

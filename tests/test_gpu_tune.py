@@ -6,6 +6,8 @@ import pytest
 import synth
 from oracle import dense
 
+from test_gpu_parity import check_point
+
 pytestmark = pytest.mark.gpu
 
 
@@ -25,13 +27,40 @@ def test_autotune_cache_round_trip_and_parity(ss, tmp_path, prec):
     dev = synth.make_device(4, 96, seed=50)[0]
     h = ss.Handle(n_b_max=4, s_b_max=96, max_points=2, max_inj=2, precision=prec)
     try:
-        nb, upd, ms = h.autotune(96, 4, cache)
-        assert nb in (8, 16) and upd in ((0,) if prec == 0 else (0, 2)) and ms > 0
-        assert cache.read_text().split()[:5] == [str(prec), "96", "4", str(nb), str(upd)]
-        assert h.autotune(96, 4, cache) == (nb, upd, pytest.approx(ms))
+        nb, nbo, upd, ms = h.autotune(96, 4, cache)
+        assert nb in (8, 16) and ms > 0
+        assert (nbo, upd) in ([(0, 0)] if prec == 0 else [(0, 0), (0, 2), (64, 2)])
+        assert cache.read_text().split()[:6] == [str(prec), "96", "4", str(nb), str(nbo), str(upd)]
+        assert h.autotune(96, 4, cache) == (nb, nbo, upd, pytest.approx(ms))
         h.set_device(0, dev)
         T, err, st, _ = h.transmission([0.2, -0.4], [0, 0])
     finally:
         h.close()
     for p, E in enumerate([0.2, -0.4]):
         assert dense.rel_T_err(float(T[p]), dense.solve_point(dev, E)["T"]) < 1e-9
+
+
+# Forced LU blockings (a cache line is read back without timing): one- and
+# two-level, outer widths that do and do not divide s_b = 300, and the
+# two-level scheme with FP64 outer updates.
+@pytest.mark.parametrize("prec,nb,nbo,upd", [(3, 16, 0, 2), (3, 8, 64, 2), (3, 16, 128, 2), (3, 8, 256, 2),
+                                             (3, 16, 64, 0), (0, 16, 64, 0)])
+def test_forced_blocking_parity(ss, tmp_path, prec, nb, nbo, upd):
+    s_b, n_b = 300, 3
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{prec} {s_b} 4 {nb} {nbo} {upd} 1.0\n")
+    dev = synth.make_device(n_b, s_b, seed=51)[0]
+    inj = synth.make_injection(s_b, 3, seed=52, n_pts=2)
+    Es = [0.15, -0.35]
+    h = ss.Handle(n_b_max=n_b, s_b_max=s_b, max_points=2, max_inj=3, precision=prec)
+    try:
+        assert h.autotune(s_b, 4, cache) == (nb, nbo, upd, pytest.approx(1.0))
+        h.set_device(0, dev)
+        sL, sR, _, st0, _ = h.self_energy(Es, [0, 0])
+        xs, st, _ = h.solve(Es, [0, 0], [inj[0], inj[1]])
+        T, err, st2, _ = h.transmission(Es, [0, 0])
+    finally:
+        h.close()
+    assert np.all(st0 == 0) and np.all(st == 0) and np.all(st2 == 0)
+    for p, E in enumerate(Es):
+        check_point({"sL": sL, "sR": sR, "T": T, "x": xs}, p, dev, E, inj[p])

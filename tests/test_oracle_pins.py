@@ -274,3 +274,35 @@ def test_adam_constant_gradient_closed_form():
         p, m, v = mlp.adam_step(p, g, m, v, t, lr=0.01)
         step = prev - p[0]
         assert np.allclose(step, 0.01 * g[0] / (np.abs(g[0]) + 1e-8), rtol=1e-12)
+
+
+def test_backward_error_is_the_smallest_perturbation():
+    """Rigal-Gaches: the perturbation dM = -t r x^H / ||x||^2 * a, db = t r * c
+    with a = ||M|| ||x|| / (||M|| ||x|| + ||b||), c = ||b|| / (...) makes x an
+    exact solution and has ||dM|| = eta ||M||, ||db|| = eta ||b||."""
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((7, 7)) + 1j * rng.standard_normal((7, 7))
+    x = rng.standard_normal((7, 2)) + 1j * rng.standard_normal((7, 2))
+    b = rng.standard_normal((7, 2)) + 1j * rng.standard_normal((7, 2))
+    eta = dense.backward_error(M, x, b)
+    nM, nx, nb = np.linalg.norm(M), np.linalg.norm(x), np.linalg.norm(b)
+    r = b - M @ x
+    # x is a matrix: use the minimum-norm dM with dM x = a r (Frobenius)
+    a, c = nM * nx / (nM * nx + nb), nb / (nM * nx + nb)
+    dM = a * r @ np.linalg.pinv(x)
+    db = -c * r
+    assert np.allclose((M + dM) @ x, b + db, atol=1e-12)
+    assert np.linalg.norm(db) == pytest.approx(eta * nb, rel=1e-12)
+    # for a single right-hand side the minimum-norm dM is rank one with norm eta ||M||
+    x1, b1 = x[:, :1], b[:, :1]
+    e1 = dense.backward_error(M, x1, b1)
+    r1 = b1 - M @ x1
+    n1 = np.linalg.norm(M) * np.linalg.norm(x1) + np.linalg.norm(b1)
+    dM1 = (np.linalg.norm(M) * np.linalg.norm(x1) / n1) * r1 @ x1.conj().T / np.linalg.norm(x1) ** 2
+    assert np.allclose((M + dM1) @ x1, b1 - (np.linalg.norm(b1) / n1) * r1, atol=1e-12)
+    assert np.linalg.norm(dM1) == pytest.approx(e1 * np.linalg.norm(M), rel=1e-12)
+    # closed form: M = I, b = 0 -> ||x|| / (sqrt(N) ||x||)
+    assert dense.backward_error(np.eye(9), np.ones((9, 1)), np.zeros((9, 1))) == pytest.approx(1 / 3, rel=1e-15)
+    # an exact solution has zero backward error
+    M2 = np.diag([1.0, 2.0, 4.0])
+    assert dense.backward_error(M2, np.array([[1.0], [0.5], [0.25]]), np.ones((3, 1))) == 0.0
