@@ -1308,7 +1308,10 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   cudaError_t e = cudaMalloc(&W0, tot * sizeof(z64));
   if (e == cudaSuccess) e = cudaMalloc(&piv, (size_t)n_problems * s_b * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&info, (size_t)n_problems * sizeof(int));
-  if (e != cudaSuccess) { cudaFree(W); cudaFree(W0); cudaFree(piv); return cuda_fail(h, e, "autotune buffer"); }
+  if (e != cudaSuccess) {
+    cudaFree(W); cudaFree(W0); cudaFree(piv); cudaFree(info);
+    return cuda_fail(h, e, "autotune buffer");
+  }
   {
     std::vector<z64> host(tot);
     unsigned long long r = 12345;
@@ -1329,8 +1332,8 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     cands.push_back({nb, 0, (int)Plan::UPD_FP64, 0.0});
     if (h->mixed()) {
       cands.push_back({nb, 0, (int)Plan::UPD_EXACT_TC, 0.0});
-      for (int nbo : {64, 128, 256})
-        if (nbo < s_b) cands.push_back({nb, nbo, (int)Plan::UPD_EXACT_TC, 0.0});
+      for (int nbo : {32, 64, 128, 256})
+        if (nbo < s_b && nbo > nb) cands.push_back({nb, nbo, (int)Plan::UPD_EXACT_TC, 0.0});
     }
   }
   ss_handle::Tune best{-1, 0, 0, 0.0};

@@ -23,6 +23,8 @@
 // A zero or non-finite pivot records 1 + its column in *info (first one
 // only) and the elimination continues with a zero reciprocal, so no problem
 // can stall the group.
+#include <cooperative_groups.h>
+
 #include "ss_internal.cuh"
 
 namespace ss {
@@ -247,6 +249,159 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) lu_panel_reg_kernel(const Lu
     }
 }
 
+// Cluster panel: the panel of one problem is spread over a cluster of CL
+// CTAs (CL SMs), because a single SM retires only about two FP64 FMAs per
+// clock.  Row k0 + c + CL t lives in thread t of cluster rank c, in
+// registers.  Per column one cluster barrier: before it every CTA publishes
+// its local pivot candidate (modulus, row, the row's values) and the owner of
+// the diagonal row publishes that row, all in its own shared memory; after it
+// every CTA reads the CL candidates through distributed shared memory, picks
+// the same pivot (largest |re| + |im|, lowest row on ties) and swaps and
+// updates its own rows.  The published slots alternate between two buffers,
+// so a slot is rewritten only after every CTA has passed the next barrier.
+// Same arithmetic, in the same order, as the single-CTA kernels.
+template <int NB>
+struct ClusterPanelShared {
+  double cval[2];
+  int cidx[2], cbad[2];
+  z64 cand_row[2][NB];
+  z64 diag_row[2][NB];
+  z64 prow[NB], crow[NB];
+  double wv[4];
+  int wi[4], wb[4];
+  int piv;
+};
+
+template <int NB, int CL, int NT>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluster_kernel(
+    const LuDesc* __restrict__ descs, int k0, int nb) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const LuDesc d = descs[blockIdx.x / CL];
+  __shared__ ClusterPanelShared<NB> sh;
+  const bool live = !(d.active && __ldg(d.active) == 0) && k0 < d.s;  // same for the whole cluster
+  if (live) {
+    const int s = d.s;
+    const int nbw = min(min(nb, NB), s - k0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row = k0 + crank + CL * tid;
+    z64* __restrict__ w = d.w;
+    const size_t ld = d.ldw;
+    z64 a[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[c] = (row < s && c < nbw) ? w[(size_t)row * ld + k0 + c] : zmk(0.0, 0.0);
+#pragma unroll
+    for (int J = 0; J < NB; ++J) {
+      if (J < nbw) {
+        const int col = k0 + J, buf = J & 1;
+        // local candidate
+        double best = -1.0;
+        int bi = s, bad = 0;
+        if (row >= col && row < s) {
+          const double v = fabs(a[J].x) + fabs(a[J].y);
+          if (!(v <= 1.7976931348623157e308)) bad = 1;
+          if (v > best) { best = v; bi = row; }
+        }
+        bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const double ov = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { sh.wv[warp] = best; sh.wi[warp] = bi; sh.wb[warp] = bad; }
+        __syncthreads();
+        if (tid == 0) {
+          double bv = sh.wv[0];
+          int bix = sh.wi[0], anyb = sh.wb[0];
+          for (int q = 1; q < NT / 32; ++q) {
+            if (sh.wv[q] > bv || (sh.wv[q] == bv && sh.wi[q] < bix)) { bv = sh.wv[q]; bix = sh.wi[q]; }
+            anyb |= sh.wb[q];
+          }
+          sh.cval[buf] = bv; sh.cidx[buf] = bix; sh.cbad[buf] = anyb;
+        }
+        __syncthreads();
+        if (row < s && row == sh.cidx[buf]) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) sh.cand_row[buf][c] = a[c];
+        }
+        if (row == col) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) sh.diag_row[buf][c] = a[c];
+        }
+        cluster.sync();
+        // global pivot from the CL candidates (every CTA computes the same)
+        if (warp == 0) {
+          double bv = -1.0;
+          int bix = s, anyb = 0;
+          if (lane < CL) {
+            const ClusterPanelShared<NB>* o = cluster.map_shared_rank(&sh, lane);
+            bv = o->cval[buf]; bix = o->cidx[buf]; anyb = o->cbad[buf];
+          }
+          anyb = __any_sync(0xffffffffu, anyb);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bix, off);
+            if (ov > bv || (ov == bv && oi < bix)) { bv = ov; bix = oi; }
+          }
+          bv = __shfl_sync(0xffffffffu, bv, 0);
+          bix = __shfl_sync(0xffffffffu, bix, 0);
+          const bool badp = anyb || !(bv > 0.0) || !isfinite(bv) || bix >= s;
+          if (bix >= s) bix = col;
+          const int cp = (bix - k0) % CL, cc = (col - k0) % CL;
+          if (lane < NB) {
+            const ClusterPanelShared<NB>* op = cluster.map_shared_rank(&sh, cp);
+            const ClusterPanelShared<NB>* oc = cluster.map_shared_rank(&sh, cc);
+            // the winner's published candidate row is the pivot row (its own
+            // diagonal row when the pivot column has no usable entry)
+            sh.prow[lane] = (bix == col) ? oc->diag_row[buf][lane] : op->cand_row[buf][lane];
+            sh.crow[lane] = oc->diag_row[buf][lane];
+          }
+          if (lane == 0) {
+            sh.piv = bix;
+            if (crank == 0) {
+              if (badp && d.info && *d.info == 0) *d.info = col + 1;
+              d.ipiv[col] = bix;
+            }
+          }
+        }
+        __syncthreads();
+        const int p = sh.piv;
+        if (p != col) {
+          if (row == col) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[c] = sh.prow[c];
+          } else if (row == p) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[c] = sh.crow[c];
+          }
+        }
+        if (row > col && row < s) {
+          const z64 inv = zinv(sh.prow[J]);
+          const z64 l = zmul(a[J], inv);
+          a[J] = l;
+#pragma unroll
+          for (int c = J + 1; c < NB; ++c) {
+            const z64 u = sh.prow[c];
+            a[c].x = fma(-l.x, u.x, a[c].x);
+            a[c].x = fma(l.y, u.y, a[c].x);
+            a[c].y = fma(-l.x, u.y, a[c].y);
+            a[c].y = fma(-l.y, u.x, a[c].y);
+          }
+        }
+      }
+    }
+    if (row < s) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nbw) w[(size_t)row * ld + k0 + c] = a[c];
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 constexpr int RB_THREADS = 128;
 
 // Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
@@ -378,7 +533,12 @@ int lu_panel_width(int smax) {
 void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st) {
   if (nprob <= 0) return;
   const int h = smax - k0;  // rows of the tallest panel in the group
-  if (nb <= 16 && h <= PANEL_THREADS) lu_panel_reg_kernel<16, 1><<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
+  constexpr int CL = 8;
+  if (nb == 16 && h <= CL * 64) lu_panel_cluster_kernel<16, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb);
+  else if (nb == 16 && h <= CL * 128) lu_panel_cluster_kernel<16, CL, 128><<<nprob * CL, 128, 0, st>>>(d, k0, nb);
+  else if (nb == 8 && h <= CL * 64) lu_panel_cluster_kernel<8, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb);
+  else if (nb == 8 && h <= CL * 128) lu_panel_cluster_kernel<8, CL, 128><<<nprob * CL, 128, 0, st>>>(d, k0, nb);
+  else if (nb <= 16 && h <= PANEL_THREADS) lu_panel_reg_kernel<16, 1><<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
   else if (nb <= 8 && h <= 2 * PANEL_THREADS) lu_panel_reg_kernel<8, 2><<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
   else lu_panel_kernel<<<nprob, PANEL_THREADS, 0, st>>>(d, k0, nb);
 }

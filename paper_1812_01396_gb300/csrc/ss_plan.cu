@@ -246,12 +246,12 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
     if (upd == UPD_EXACT_TC) ok = ok && oz_gemm(g, pack, cap, err, true);
     else gemm(g, upd == UPD_FP32, upd == UPD_FP64);
   };
-  const size_t off = push_vec(ds);
   const int np = (int)ds.size();
   int smax = 0;
   for (auto& d : ds) smax = std::max(smax, d.s);
   if (nb <= 0) nb = lu_panel_width(smax);
   if (nbo > 0 && (nbo <= nb || nbo % nb != 0)) nbo = 0;
+  const size_t off = push_vec(ds);
   // C -= A B with A at (ar, ac), B at (br, bc), C at (cr, cc) of the problem's W
   auto upd_desc = [](const LuDesc& d, int m, int n, int k, int ar, int ac, int br, int bc, int cr, int cc) {
     GemmDesc q{};
