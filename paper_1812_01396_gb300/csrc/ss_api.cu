@@ -237,8 +237,6 @@ int cuda_fail(ss_handle* h, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
   } while (0)
 
-// A group of large GEMMs: FP64 kernel, or the split-BF16 tensor-core kernel
-// in the mixed modes.
 // A group of large GEMMs: the FP64 kernel, or in the mixed mode the
 // FP64-accurate digit-sliced kernel on the tensor cores.
 bool big_gemm(ss_handle* h, Plan& P, const std::vector<GemmDesc>& g) {
@@ -537,22 +535,24 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
   }
   B.form(f0);
   big_gemm(h, B, gR);
-  B.gemm(gb1);
-  B.gemm(gb2);
-  B.gemm(gsb);
+  big_gemm(h, B, gb1);
+  big_gemm(h, B, gb2);
+  big_gemm(h, B, gsb);
   ::lu(h, B, lu);
-  B.gemm(gG1);
-  B.gemm(gG2);
+  big_gemm(h, B, gG1);
+  big_gemm(h, B, gG2);
   B.form(fc);
-  B.gemm(gx1);
-  B.gemm(gx2);
+  big_gemm(h, B, gx1);
+  big_gemm(h, B, gx2);
   B.form(fg);
-  B.gemm(gM);
+  big_gemm(h, B, gM);
   B.trace(tr);
 }
 
 // ------------------------------------------------------------ refinement
-// Residual r = Inj - (A - Sigma) x in FP64 for every block, and ||r||_F^2.
+// Residual r = Inj - (A - Sigma) x for every block, and ||r||_F^2 and
+// ||x||_F^2.  The products are FP64-accurate (FP64 SIMT, or the exact
+// digit-sliced tensor-core GEMM in the mixed mode).
 void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr, double* xx) {
   Plan& R = h->p_ir_res;
   R.clear();
@@ -591,11 +591,11 @@ void build_ir_residual(ss_handle* h, std::vector<PW>& pts, int ninj, double* rr,
     nr.push_back({w.x, ninj, n * s, ninj, xx + p, nullptr});
   }
   R.form(f);
-  R.gemm(gd);
-  R.gemm(gu);
-  R.gemm(gl);
-  R.gemm(gs1);
-  R.gemm(gs2);
+  big_gemm(h, R, gd);
+  big_gemm(h, R, gu);
+  big_gemm(h, R, gl);
+  big_gemm(h, R, gs1);
+  big_gemm(h, R, gs2);
   R.frob2(nr);
 }
 
@@ -634,8 +634,9 @@ void build_ir_norms(Plan& N, std::vector<PW>& pts, int ninj, double* mm, double*
 
 // Correction delta = M~^-1 r with the stored D_i^-1 (block UL substitution of
 // the first-column sweep) and R^-1 (Sherman-Morrison-Woodbury), then x += delta.
-// FP64 products: with FP32 ones the correction stops contracting on long
-// devices (its error times the condition number of A - Sigma nears 1).
+// FP64-accurate products (the exact tensor-core GEMM): with FP32 ones the
+// correction stops contracting on long devices (its error times the condition
+// number of A - Sigma nears 1).
 void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax) {
   Plan& C = h->p_ir_cor;
   C.clear();
@@ -662,8 +663,8 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
       }
     }
     C.form(f);
-    C.gemm(g1);
-    C.gemm(g2);
+    big_gemm(h, C, g1);
+    big_gemm(h, C, g2);
   }
   // forward: y_1 = w_1 ; y_i = w_i - Di^-1 (U_{i-1}^H y_{i-1})  (in place in w)
   for (int t = 1; t < nmax; ++t) {
@@ -679,8 +680,8 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
                          plain(wi - bs, ninj), w.tv, ninj, ONE, ZERO));
       g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, MONE, ONE));
     }
-    C.gemm(g1);
-    C.gemm(g2);
+    big_gemm(h, C, g1);
+    big_gemm(h, C, g2);
   }
   // SMW: z' = R^-1 [Sigma_L y_1 ; Sigma_R y_n] ; x_i += y_i + Q_i z'_top + P_i z'_bot
   std::vector<GemmDesc> gz1, gz2, gr, gx1, gx2;
@@ -701,12 +702,12 @@ void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax)
       gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.tv + bs, ninj), xi, ninj, ONE, ONE));
     }
   }
-  C.gemm(gz1);
-  C.gemm(gz2);
-  C.gemm(gr);
+  big_gemm(h, C, gz1);
+  big_gemm(h, C, gz2);
+  big_gemm(h, C, gr);
   C.form(fx);
-  C.gemm(gx1);
-  C.gemm(gx2);
+  big_gemm(h, C, gx1);
+  big_gemm(h, C, gx2);
   (void)P;
 }
 
@@ -924,6 +925,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
         // ||r|| / (||A - Sigma|| ||x|| + ||Inj||) (Frobenius norms) is <= ir_tol
         build_ir_residual(h, pts, want.ninj, rr, xx);
         build_ir_correction(h, pts, want.ninj, nmax);
+        if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the refinement");
         Plan nrm;
         build_ir_norms(nrm, pts, want.ninj, mm, bb);
         CK(nrm.upload(st), "upload");

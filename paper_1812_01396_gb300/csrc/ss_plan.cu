@@ -40,6 +40,35 @@ size_t Plan::oz_pack_bytes(const std::vector<GemmDesc>& ds) {
 
 bool Plan::oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label) {
   if (ds.empty()) return true;
+  if (oz_pack_bytes(ds) <= cap) return oz_gemm_group(ds, pack, cap, err, lu_label);
+  // the digit slices of the whole group do not fit: consecutive chunks that
+  // do, one after the other (the GEMMs of a group are independent)
+  std::vector<GemmDesc> chunk;
+  std::map<OpKey, int> seen;
+  size_t bytes = 0;
+  for (const GemmDesc& g : ds) {
+    const OpKey ka{g.a.p, g.a.s, g.a.e.x, g.a.e.y, g.a.ld, g.a.trans, g.m, g.k, 0};
+    const OpKey kb{g.b.p, g.b.s, g.b.e.x, g.b.e.y, g.b.ld, g.b.trans, 2 * g.n, g.k, 1};
+    const size_t need = (seen.count(ka) ? 0 : oz_operand_bytes(g.m, g.m, g.k)) +
+                        (seen.count(kb) ? 0 : oz_operand_bytes(2 * g.n, g.n, g.k));
+    if (bytes + need > cap) {
+      if (chunk.empty()) return false;  // a single GEMM does not fit
+      if (!oz_gemm_group(chunk, pack, cap, err, lu_label)) return false;
+      chunk.clear();
+      seen.clear();
+      bytes = oz_operand_bytes(g.m, g.m, g.k) + oz_operand_bytes(2 * g.n, g.n, g.k);
+    } else {
+      bytes += need;
+    }
+    seen[ka] = 1;
+    seen[kb] = 1;
+    chunk.push_back(g);
+  }
+  return oz_gemm_group(chunk, pack, cap, err, lu_label);
+}
+
+bool Plan::oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err,
+                         bool lu_label) {
   std::map<OpKey, int> index;
   std::vector<OzPackDesc> pk;
   std::vector<CUtensorMap> maps;

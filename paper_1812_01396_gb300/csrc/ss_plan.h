@@ -118,6 +118,7 @@ class Plan {
   static size_t tc_pack_bytes(const std::vector<GemmDesc>& ds, int mode);
   // FP64-accurate complex GEMMs on the tensor cores (digit-sliced BF16, exact
   // FP32 accumulation); operands sliced into `pack` as for tc_gemm.
+  // Groups whose slices exceed `cap` are issued as consecutive chunks.
   bool oz_gemm(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label = false);
   static size_t oz_pack_bytes(const std::vector<GemmDesc>& ds);
   // Blocked LU + solve of every problem in ds (panel width nb <= 32; nb <= 0
@@ -185,6 +186,7 @@ class Plan {
   bool empty() const { return recs_.empty(); }
 
  private:
+  bool oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label);
   void release();
   void destroy_graph();
   std::vector<unsigned char> host_;
