@@ -25,8 +25,9 @@
 //
 // Levels d <= S - 1 are kept (the dropped ones are below 2^-54 of the
 // largest product), so the result matches an FP64 GEMM to rounding.
-// One CTA per 128 x 64 tile of C' = A' B'^T; warp 0 issues TMA, warp 1 the
-// MMAs, warps 2-5 drain the accumulators.  Every wait is bounded (2 s).
+// Persistent CTAs over 128 x 128 tiles of C' = A' B'^T; warp 0 issues TMA,
+// warp 1 the MMAs, warps 2-9 drain the accumulators.  Every wait is bounded
+// (2 s).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -39,12 +40,22 @@ namespace ss {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64, STAGES = 6, NACC = 4;
-constexpr int OZ_THREADS = 192;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6, NACC = 4;
+// Tiles of a problem are visited in groups of GM row tiles (column-major
+// inside a group), so the CTAs running at the same time share A row panels
+// and B column panels and their digit slices stay in L2.
+constexpr int GM = 8;
+// warp 0: TMA, warp 1: MMA, warps 2-9: epilogue (two warps per TMEM lane
+// quadrant, each draining half of the tile's columns: 32 complex columns,
+// 64 int64 fixed-point sums per thread).  Ten warps keep three warps per
+// SM sub-partition, so a thread may hold 168 registers.
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // real columns per epilogue thread
+constexpr int OZ_THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t A_BYTES = BM * BK * 2;
 constexpr uint32_t B_BYTES = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 256;  // NACC accumulators of BN columns
+constexpr uint32_t TMEM_COLS = NACC * BN;  // NACC accumulators of BN columns (512 = all of TMEM)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -70,10 +81,12 @@ __device__ __forceinline__ bool oz_tile(const OzDesc* __restrict__ descs, const 
   pid = find_problem(tile_start, nprob, tile);
   const OzDesc& d = descs[pid];
   if (d.active && __ldg(d.active) == 0) return false;
-  const int tiles_n = (d.n2 + BN - 1) / BN;
+  const int tiles_n = (d.n2 + BN - 1) / BN, tiles_m = (d.m + BM - 1) / BM;
   const int t = tile - __ldg(tile_start + pid);
-  m0 = (t / tiles_n) * BM;
-  n0 = (t % tiles_n) * BN;
+  const int group = t / (GM * tiles_n), first = group * GM;
+  const int gm = min(GM, tiles_m - first), r = t - group * GM * tiles_n;
+  m0 = (first + r % gm) * BM;
+  n0 = (r / gm) * BN;
   return true;
 }
 
@@ -94,7 +107,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
-    for (int i = 0; i < NACC; ++i) { mbar_init(&accf_bar[i], 1); mbar_init(&acce_bar[i], 128); }
+    for (int i = 0; i < NACC; ++i) { mbar_init(&accf_bar[i], 1); mbar_init(&acce_bar[i], 32 * EPI_WARPS); }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -174,7 +187,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
     // (|total| < 2^24 * 1.1 * 2^37 < 2^62): levels with beta*d <= 37 are
     // exact, deeper ones round by at most half a unit of 2^-37, so FP64
     // arithmetic is needed only once per output element.
-    const int q4 = warp & 3;
+    const int q4 = warp & 3;             // TMEM lanes 32 q4 .. 32 q4 + 31
+    const int part = (warp - 2) >> 2;    // real columns EPI_COLS part .. of the tile
+    static_assert(EPI_COLS % 16 == 0, "16-column TMEM loads");
     int pg = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       int pid, m0, n0;
@@ -185,10 +200,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
         const int j = (n0 >> 1) + (threadIdx.x - 64);
         colscale[threadIdx.x - 64] = (2 * j < d.n2) ? pow2(exp_of(d.mB[j])) : 0.0;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // epilogue warps only
-      long long re[BN / 2], im[BN / 2];
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");  // epilogue warps only
+      long long re[EPI_COLS / 2], im[EPI_COLS / 2];
 #pragma unroll
-      for (int e = 0; e < BN / 2; ++e) { re[e] = 0; im[e] = 0; }
+      for (int e = 0; e < EPI_COLS / 2; ++e) { re[e] = 0; im[e] = 0; }
       bool ok = true;
       for (int p = 0; p < d.npass; ++p, ++pg) {
         const int acc = pg % NACC, use = pg / NACC;
@@ -197,32 +212,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
         const int sh = 37 - d.beta_bits * d.pd[p];  // shift of this level into the fixed point
         if (ok && !s_fail) {
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + half * 32);
+          for (int sub = 0; sub < EPI_COLS / 16; ++sub) {
+            uint32_t v[16];
+            const uint32_t taddr =
+                tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + part * EPI_COLS + sub * 16);
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                  "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (sh >= 0) {
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                re[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
-                im[half * 16 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
+              for (int e = 0; e < 8; ++e) {
+                re[sub * 8 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
+                im[sub * 8 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
               }
             } else {
               const int rs = -sh;
               const long long rnd = 1ll << (rs - 1);
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                re[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
-                im[half * 16 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
+              for (int e = 0; e < 8; ++e) {
+                re[sub * 8 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
+                im[sub * 8 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
               }
             }
           }
@@ -235,10 +248,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
         const double rs_row = pow2(exp_of(d.mA[row]) - 37 - 2 * d.beta_bits);
         const bool unit_alpha = d.alpha.y == 0.0 && (d.alpha.x == 1.0 || d.alpha.x == -1.0);
 #pragma unroll
-        for (int e = 0; e < BN / 2; ++e) {
-          const int j = (n0 >> 1) + e;
+        for (int e = 0; e < EPI_COLS / 2; ++e) {
+          const int j = (n0 >> 1) + part * (EPI_COLS / 2) + e;
           if (2 * j < d.n2) {
-            const double sc = rs_row * colscale[e];
+            const double sc = rs_row * colscale[part * (EPI_COLS / 2) + e];
             z64 out = zmk((double)re[e] * sc, (double)im[e] * sc);
             if (unit_alpha) { if (d.alpha.x < 0.0) { out.x = -out.x; out.y = -out.y; } }
             else out = zmul(d.alpha, out);
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
           }
         }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // colscale is rewritten for the next tile
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");  // colscale is rewritten next tile
     }
   }
   __syncthreads();

@@ -31,17 +31,24 @@ static __device__ __forceinline__ unsigned long long global_ns() {
 
 // Bounded wait on the phase with the given parity; returns false after
 // WAIT_NS of wall time without completion.
+static __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// The clock is read only once the first try fails, so a phase that has
+// already completed costs one try_wait.
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
+  if (mbar_try_wait(a, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
+    if (mbar_try_wait(a, parity)) return true;
     if (global_ns() - t0 > WAIT_NS) return false;
   }
 }
