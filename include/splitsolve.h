@@ -193,10 +193,12 @@ const char* ss_noalloc_last_error(void);
 
 /* Autotune the block LU-solve used by every sweep, doubling step and boundary
  * solve of blocks of size s_b: times a synthetic batch of n_problems
- * systems [D | B] (s_b x 2 s_b) for each panel width (8 and 16, or 32 above
+ * systems [D | B] (s_b x 3 s_b, the shape of the doubling and sweep
+ * systems) for each panel width (8 and 16, or 32 above
  * s_b = 512) and, in SS_MIXED_OZAKI, each update arithmetic (0: FP64 SIMT,
- * 2: exact tensor-core products) with one-level blocking or two-level
- * blocking of outer width 32, 64, 128 or 256 (below s_b), and keeps the fastest
+ * 2: exact tensor-core products for the deep updates, 3: for every update)
+ * with one-level blocking or two-level blocking of outer width 32, 64, 128
+ * or 256 (below s_b), and keeps the fastest
  * for this handle.  The factorisation is the block LU of Sec. 3B; the choice
  * changes the order of FP64 roundings only.
  * cache_path (optional): a text file of lines "precision s_b n_problems nb

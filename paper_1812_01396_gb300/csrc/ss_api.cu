@@ -1301,7 +1301,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   }
   // synthetic batch of [D | B] systems, D diagonally weighted so the
   // factorisation is well posed; a pristine copy restores it between runs
-  const size_t per = (size_t)s_b * 2 * s_b;
+  const size_t per = (size_t)s_b * 3 * s_b;  // [D | B], B of 2 s_b columns like the doubling and sweeps
   const size_t tot = per * n_problems;
   z64 *W = nullptr, *W0 = nullptr;
   int *piv = nullptr, *info = nullptr;
@@ -1325,7 +1325,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
       host[i] = make_double2(a, b);
     }
     for (int p = 0; p < n_problems; ++p)
-      for (int i = 0; i < s_b; ++i) host[p * per + (size_t)i * 2 * s_b + i].x += 4.0;
+      for (int i = 0; i < s_b; ++i) host[p * per + (size_t)i * 3 * s_b + i].x += 4.0;
     e = cudaMemcpy(W0, host.data(), tot * sizeof(z64), cudaMemcpyHostToDevice);
   }
   std::vector<ss_handle::Tune> cands;
@@ -1335,7 +1335,8 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     if (h->mixed()) {
       cands.push_back({nb, 0, (int)Plan::UPD_EXACT_TC, 0.0});
       for (int nbo : {32, 64, 128, 256})
-        if (nbo < s_b && nbo > nb) cands.push_back({nb, nbo, (int)Plan::UPD_EXACT_TC, 0.0});
+        if (nbo < s_b && nbo > nb)
+          for (int u : {(int)Plan::UPD_EXACT_TC, (int)Plan::UPD_EXACT_ALL}) cands.push_back({nb, nbo, u, 0.0});
     }
   }
   ss_handle::Tune best{-1, 0, 0, 0.0};
@@ -1347,7 +1348,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     std::vector<LuDesc> ds;
     for (int p = 0; p < n_problems; ++p) {
       LuDesc L{};
-      L.w = W + p * per; L.ldw = 2 * s_b; L.s = s_b; L.ncols = 2 * s_b; L.ipiv = piv + (size_t)p * s_b; L.info = info + p;
+      L.w = W + p * per; L.ldw = 3 * s_b; L.s = s_b; L.ncols = 3 * s_b; L.ipiv = piv + (size_t)p * s_b; L.info = info + p;
       ds.push_back(L);
     }
     Plan P;

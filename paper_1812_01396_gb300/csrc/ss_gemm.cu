@@ -8,9 +8,10 @@
 //
 // Design: one launch covers a group of independent problems of any shapes.
 // CTA b finds its problem by binary search in a prefix table of tile counts.
-// Each CTA owns a 64 x 64 complex output tile, stages 64 x 8 slices of op(A)
-// and op(B) in shared memory and keeps a 4 x 4 complex micro-tile per thread
-// in registers.  On GB300 the FP64 pipe (about 2 DFMA per clock per SM) is the
+// Each CTA owns a TM x TN complex output tile (64 x 64, or 16 x 256 / 256 x 16
+// for the skinny updates of the blocked LU, whichever pads the group least),
+// stages TM x 8 and 8 x TN slices of op(A) and op(B) in shared memory and
+// keeps a 4 x 4 complex micro-tile per thread in registers.  On GB300 the FP64 pipe (about 2 DFMA per clock per SM) is the
 // bound by a wide margin, so the kernel spends its effort on keeping every
 // issued instruction a DFMA rather than on deep staging.
 //
@@ -21,7 +22,10 @@
 namespace ss {
 
 namespace {
-constexpr int TM = 64, TN = 64, TK = 8, NT = 256;
+constexpr int TK = 8, NT = 256;
+// tile shapes by variant: 0: 64 x 64, 1: 16 x 256, 2: 256 x 16
+__host__ __device__ constexpr int tile_m(int v) { return v == 1 ? 16 : (v == 2 ? 256 : 64); }
+__host__ __device__ constexpr int tile_n(int v) { return v == 1 ? 256 : (v == 2 ? 16 : 64); }
 
 __device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, int nprob, int bid) {
   int lo = 0, hi = nprob - 1;
@@ -58,9 +62,11 @@ struct Cx<float> {
 // R = double: the FP64 kernel of the FP64 path.  R = float: operands are
 // rounded to FP32 on load and accumulated in FP32 (the low-rank LU updates of
 // the mixed path); C is still read and written in FP64.
-template <typename R>
+template <typename R, int V>
 __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ descs,
                                                    const int* __restrict__ tile_start, int nprob) {
+  constexpr int TM = tile_m(V), TN = tile_n(V), TY = TM / 4, TX = TN / 4;
+  static_assert(TY * TX == NT, "one thread per 4 x 4 micro-tile");
   typedef typename Cx<R>::T CT;
   __shared__ CT As[TK][TM];
   __shared__ CT Bs[TK][TN];
@@ -72,7 +78,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const int t = blockIdx.x - __ldg(tile_start + pid);
   const int row0 = (t / tiles_n) * TM, col0 = (t % tiles_n) * TN;
   const Operand a = d.a, b = d.b;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
 
   CT acc[4][4];
 #pragma unroll
@@ -98,9 +104,9 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
     for (int kk = 0; kk < TK; ++kk) {
       CT av[4], bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TX * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -118,11 +124,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int r = row0 + ty + 16 * i;
+    const int r = row0 + ty + TY * i;
     if (r >= m) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = col0 + tx + 16 * j;
+      const int c = col0 + tx + TX * j;
       if (c >= n) continue;
       z64 v = zmul(alpha, Cx<R>::back(acc[i][j]));
       if (d.cmode == 1) {
@@ -139,21 +145,36 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
 }
 }  // namespace
 
-int zgemm_tiles(int m, int n) {
+int zgemm_tiles(int m, int n, int variant) {
   if (m <= 0 || n <= 0) return 0;
-  return ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
+  const int tm = tile_m(variant), tn = tile_n(variant);
+  return ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
 }
 
-void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
-                  cudaStream_t st) {
+int zgemm_variant(const std::vector<GemmDesc>& ds) {
+  // the tile shape that pads the group's work least (ties: 64 x 64)
+  double best = 0.0;
+  int bv = 0;
+  for (int v = 0; v < 3; ++v) {
+    double work = 0.0;
+    for (auto& g : ds) work += (double)zgemm_tiles(g.m, g.n, v) * tile_m(v) * tile_n(v);
+    if (v == 0 || work < best) { best = work; bv = v; }
+  }
+  return bv;
+}
+
+void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles, cudaStream_t st,
+                  int variant) {
   if (nprob <= 0 || total_tiles <= 0) return;
-  zgemm_kernel<double><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  if (variant == 1) zgemm_kernel<double, 1><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  else if (variant == 2) zgemm_kernel<double, 2><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  else zgemm_kernel<double, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
 }
 
 void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
                     cudaStream_t st) {
   if (nprob <= 0 || total_tiles <= 0) return;
-  zgemm_kernel<float><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  zgemm_kernel<float, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
 }
 
 }  // namespace ss

@@ -111,9 +111,12 @@ struct TraceDesc {  // out = sum_{a,b} A[a,b] * B[b,a]
 // --------------------------------------------------------------- launchers
 // Each launcher takes device arrays of descriptors plus the host-known grid
 // sizes; all are asynchronous on `st`.
+// variant: tile shape (0: 64 x 64, 1: 16 x 256, 2: 256 x 16); tile_start
+// must be built with zgemm_tiles of the same variant.
 void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
-                  cudaStream_t st);
-int zgemm_tiles(int m, int n);  // CTAs one problem needs
+                  cudaStream_t st, int variant = 0);
+int zgemm_tiles(int m, int n, int variant = 0);  // CTAs one problem needs
+int zgemm_variant(const std::vector<GemmDesc>& ds);  // tile shape padding the group least
 // Same descriptors, FP32 arithmetic (operands rounded to FP32 on load, FP32
 // accumulation, FP64 C): the low-rank LU updates of the mixed path.
 void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,

@@ -272,8 +272,13 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
-    if (upd == UPD_EXACT_TC) ok = ok && oz_gemm(g, pack, cap, err, true);
+    if (upd == UPD_EXACT_TC || upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
     else gemm(g, upd == UPD_FP32, upd == UPD_FP64);
+  };
+  // the nb-deep updates inside an outer block (two-level blocking)
+  auto inner_update = [&](const std::vector<GemmDesc>& g) {
+    if (upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
+    else gemm(g, false, true);
   };
   const int np = (int)ds.size();
   int smax = 0;
@@ -338,7 +343,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
           g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, k0 + nbw, k0 + nbw, k0 + nbw));
         }
         rowblock(k0, 0, maxc);
-        gemm(g, false, true);
+        inner_update(g);
       }
       // the block's rows on the columns right of it
       for (int k0 = K0; k0 < kend; k0 += nb) {
@@ -353,7 +358,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
           g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, K1, k0 + nbw, K1));
         }
         rowblock(k0, 1, maxc);
-        gemm(g, false, true);
+        inner_update(g);
       }
       // one trailing update of depth nbo
       std::vector<GemmDesc> g;
@@ -396,7 +401,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
         const int nbw = std::min(nb, d.s - k0);
         g.push_back(upd_desc(d, k0 - K0, d.ncols - d.s, nbw, K0, k0, k0, d.s, K0, d.s));
       }
-      gemm(g, false, true);
+      inner_update(g);
     } else {
       // every row above the outer block, depth nbo
       for (auto& d : ds) {
@@ -498,7 +503,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
     const int* t = reinterpret_cast<const int*>(dev_ + r.toff);
     switch (r.kind) {
       case K_GEMM:
-      case K_GEMM_LU: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
+      case K_GEMM_LU: launch_zgemm((const GemmDesc*)d, t, r.nprob, r.tiles, st, r.ival); ++n; break;
       case K_OZSCALE: launch_oz_scale((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_OZPACK: launch_oz_pack((const OzPackDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_OZGEMM:

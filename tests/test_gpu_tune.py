@@ -29,7 +29,7 @@ def test_autotune_cache_round_trip_and_parity(ss, tmp_path, prec):
     try:
         nb, nbo, upd, ms = h.autotune(96, 4, cache)
         assert nb in (8, 16) and ms > 0
-        assert (nbo, upd) in ([(0, 0)] if prec == 0 else [(0, 0), (0, 2), (32, 2), (64, 2)])
+        assert (nbo, upd) in ([(0, 0)] if prec == 0 else [(0, 0), (0, 2), (32, 2), (64, 2), (32, 3), (64, 3)])
         assert cache.read_text().split()[:6] == [str(prec), "96", "4", str(nb), str(nbo), str(upd)]
         assert h.autotune(96, 4, cache) == (nb, nbo, upd, pytest.approx(ms))
         h.set_device(0, dev)
@@ -41,10 +41,12 @@ def test_autotune_cache_round_trip_and_parity(ss, tmp_path, prec):
 
 
 # Forced LU blockings (a cache line is read back without timing): one- and
-# two-level, outer widths that do and do not divide s_b = 300, and the
-# two-level scheme with FP64 outer updates.
+# two-level, outer widths that do and do not divide s_b = 300, exact
+# products for the deep updates only or for all of them, and the two-level
+# scheme with FP64 outer updates.
 @pytest.mark.parametrize("prec,nb,nbo,upd", [(3, 16, 0, 2), (3, 8, 64, 2), (3, 16, 64, 2), (3, 16, 32, 2),
-                                             (3, 16, 128, 2), (3, 8, 256, 2), (3, 16, 64, 0), (0, 16, 64, 0)])
+                                             (3, 16, 128, 2), (3, 8, 256, 2), (3, 16, 64, 3), (3, 8, 32, 3),
+                                             (3, 16, 64, 0), (0, 16, 64, 0)])
 def test_forced_blocking_parity(ss, tmp_path, prec, nb, nbo, upd):
     s_b, n_b = 300, 3
     cache = tmp_path / "tune.txt"
