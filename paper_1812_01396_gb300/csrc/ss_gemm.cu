@@ -8,8 +8,9 @@
 //
 // Design: one launch covers a group of independent problems of any shapes.
 // CTA b finds its problem by binary search in a prefix table of tile counts.
-// Each CTA owns a TM x TN complex output tile (64 x 64, or 16 x 256 / 256 x 16
-// for the skinny updates of the blocked LU, whichever pads the group least),
+// Each CTA owns a TM x TN complex output tile (64 x 64, 16 x 256, 256 x 16,
+// 16 x 64 or 64 x 16: per group the shape with the least padded work per busy
+// SM, as the blocked LU's nb-deep updates are skinny and few),
 // stages TM x 8 and 8 x TN slices of op(A) and op(B) in shared memory and
 // keeps a 4 x 4 complex micro-tile per thread in registers.  On GB300 the FP64 pipe (about 2 DFMA per clock per SM) is the
 // bound by a wide margin, so the kernel spends its effort on keeping every
@@ -23,9 +24,16 @@ namespace ss {
 
 namespace {
 constexpr int TK = 8, NT = 256;
-// tile shapes by variant: 0: 64 x 64, 1: 16 x 256, 2: 256 x 16
-__host__ __device__ constexpr int tile_m(int v) { return v == 1 ? 16 : (v == 2 ? 256 : 64); }
-__host__ __device__ constexpr int tile_n(int v) { return v == 1 ? 256 : (v == 2 ? 16 : 64); }
+// tile shapes by variant (TM x TN, micro-tile MI x MJ per thread):
+//   0: 64 x 64 (4 x 4), 1: 16 x 256 (4 x 4), 2: 256 x 16 (4 x 4),
+//   3: 16 x 64 (1 x 4), 4: 64 x 16 (4 x 1).
+// The FP64 pipe, not shared memory, bounds every variant, so the small
+// tiles only trade register reuse for more CTAs on small groups.
+constexpr int NVAR = 5;
+__host__ __device__ constexpr int tile_m(int v) { return v == 1 || v == 3 ? 16 : (v == 2 ? 256 : 64); }
+__host__ __device__ constexpr int tile_n(int v) { return v == 1 ? 256 : (v == 2 || v == 4 ? 16 : 64); }
+__host__ __device__ constexpr int micro_m(int v) { return v == 3 ? 1 : 4; }
+__host__ __device__ constexpr int micro_n(int v) { return v == 4 ? 1 : 4; }
 
 __device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, int nprob, int bid) {
   int lo = 0, hi = nprob - 1;
@@ -65,8 +73,9 @@ struct Cx<float> {
 template <typename R, int V>
 __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ descs,
                                                    const int* __restrict__ tile_start, int nprob) {
-  constexpr int TM = tile_m(V), TN = tile_n(V), TY = TM / 4, TX = TN / 4;
-  static_assert(TY * TX == NT, "one thread per 4 x 4 micro-tile");
+  constexpr int TM = tile_m(V), TN = tile_n(V), MI = micro_m(V), MJ = micro_n(V);
+  constexpr int TY = TM / MI, TX = TN / MJ;
+  static_assert(TY * TX == NT, "one thread per micro-tile");
   typedef typename Cx<R>::T CT;
   __shared__ CT As[TK][TM];
   __shared__ CT Bs[TK][TN];
@@ -80,11 +89,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const Operand a = d.a, b = d.b;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
 
-  CT acc[4][4];
+  CT acc[MI][MJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { acc[i][j].x = 0; acc[i][j].y = 0; }
+    for (int j = 0; j < MJ; ++j) { acc[i][j].x = 0; acc[i][j].y = 0; }
 
   for (int k0 = 0; k0 < K; k0 += TK) {
     for (int e = tid; e < TM * TK; e += NT) {
@@ -102,15 +111,15 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      CT av[4], bv[4];
+      CT av[MI], bv[MJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + TY * i];
+      for (int i = 0; i < MI; ++i) av[i] = As[kk][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + TX * j];
+      for (int j = 0; j < MJ; ++j) bv[j] = Bs[kk][tx + TX * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < MI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < MJ; ++j) {
           acc[i][j].x = fma(av[i].x, bv[j].x, acc[i][j].x);
           acc[i][j].x = fma(-av[i].y, bv[j].y, acc[i][j].x);
           acc[i][j].y = fma(av[i].x, bv[j].y, acc[i][j].y);
@@ -123,11 +132,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const z64 alpha = d.alpha, beta = d.beta;
   const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < MI; ++i) {
     const int r = row0 + ty + TY * i;
     if (r >= m) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < MJ; ++j) {
       const int c = col0 + tx + TX * j;
       if (c >= n) continue;
       z64 v = zmul(alpha, Cx<R>::back(acc[i][j]));
@@ -152,13 +161,24 @@ int zgemm_tiles(int m, int n, int variant) {
 }
 
 int zgemm_variant(const std::vector<GemmDesc>& ds) {
-  // the tile shape that pads the group's work least (ties: 64 x 64)
+  // the tile shape with the least padded work per busy SM (ties: 64 x 64)
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 148;
+  }
   double best = 0.0;
   int bv = 0;
-  for (int v = 0; v < 3; ++v) {
-    double work = 0.0;
-    for (auto& g : ds) work += (double)zgemm_tiles(g.m, g.n, v) * tile_m(v) * tile_n(v);
-    if (v == 0 || work < best) { best = work; bv = v; }
+  for (int v = 0; v < NVAR; ++v) {
+    double work = 0.0, ctas = 0.0;
+    for (auto& g : ds) {
+      const int t = zgemm_tiles(g.m, g.n, v);
+      work += (double)t * tile_m(v) * tile_n(v);
+      ctas += t;
+    }
+    const double cost = work / std::min(ctas, (double)nsm);
+    if (v == 0 || cost < best * 0.999) { best = cost; bv = v; }
   }
   return bv;
 }
@@ -166,9 +186,13 @@ int zgemm_variant(const std::vector<GemmDesc>& ds) {
 void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles, cudaStream_t st,
                   int variant) {
   if (nprob <= 0 || total_tiles <= 0) return;
-  if (variant == 1) zgemm_kernel<double, 1><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
-  else if (variant == 2) zgemm_kernel<double, 2><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
-  else zgemm_kernel<double, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  switch (variant) {
+    case 1: zgemm_kernel<double, 1><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob); break;
+    case 2: zgemm_kernel<double, 2><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob); break;
+    case 3: zgemm_kernel<double, 3><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob); break;
+    case 4: zgemm_kernel<double, 4><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob); break;
+    default: zgemm_kernel<double, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
+  }
 }
 
 void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
