@@ -331,44 +331,65 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzPackDesc* __restr
   }
 }
 
-// Digits of x / 2^e (|x| < 2^e) for every slice, written at columns t*w + off,
-// using integer arithmetic only: the IEEE mantissa is placed in a signed
-// 62-bit fixed point R = x 2^{62-e}, then digit t is the round-to-nearest
-// quotient of R by 2^{62 - beta (t+1)} and is removed from R.
-__device__ __forceinline__ void write_digits(__nv_bfloat16* row, int w, int off, int S, int beta, double x, int e) {
+// Signed 62-bit fixed point R = x 2^{62-e} of |x| < 2^e from the IEEE bits
+// (zero and subnormals, far below any row scale here, give zero).
+__device__ __forceinline__ long long fixed62(double x, int e) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long R = 0;
-  if (ex != 0) {  // zero and subnormals (far below any row scale here) give zero digits
+  if (ex != 0) {
     const long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
     const int shift = ex - 1013 - e;  // x 2^{62-e} = m 2^{ex-1075+62-e}
     if (shift >= 0) R = m << shift;   // shift <= 9 because |x| < 2^e
     else if (shift > -64) R = (m + (1ll << (-shift - 1))) >> (-shift);
     if (bits >> 63) R = -R;
   }
+  return R;
+}
+
+// Digit t of R is the round-to-nearest quotient by 2^{62 - beta (t+1)}, then
+// removed from R; |digit| <= 2^beta is an exact BF16 number.  Two values
+// (adjacent columns) at a time, stored as one bfloat16 pair per slice.
+template <int S>
+__device__ __forceinline__ void write_digits2(__nv_bfloat16* row, int w, int off, int beta, double x0, double x1,
+                                              int e) {
+  long long R0 = fixed62(x0, e), R1 = fixed62(x1, e);
+#pragma unroll 3
+  for (int t = 0; t < S; ++t) {
+    const int sh = 62 - beta * (t + 1);
+    const long long h = 1ll << (sh - 1);
+    const long long q0 = (R0 + h) >> sh, q1 = (R1 + h) >> sh;
+    R0 -= q0 << sh;
+    R1 -= q1 << sh;
+    *reinterpret_cast<__nv_bfloat162*>(row + (size_t)t * w + off) =
+        __floats2bfloat162_rn((float)(int)q0, (float)(int)q1);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void write_digits1(__nv_bfloat16* row, int w, int off, int beta, double x, int e) {
+  long long R = fixed62(x, e);
+#pragma unroll 3
   for (int t = 0; t < S; ++t) {
     const int sh = 62 - beta * (t + 1);
     const long long q = (R + (1ll << (sh - 1))) >> sh;
     R -= q << sh;
-    row[(size_t)t * w + off] = __float2bfloat16_rn((float)q);
+    row[(size_t)t * w + off] = __float2bfloat16_rn((float)(int)q);
   }
 }
 
 // Digit slices of a 32 x 32 tile (coalesced loads into shared memory, then
-// rows of the packed matrix written along the inner index), or, for the
-// tiles past the data, the zero padding of every slice.
-__global__ void __launch_bounds__(256) oz_pack_kernel(const OzPackDesc* __restrict__ descs,
-                                                      const int* __restrict__ tile_start, int nprob) {
-  const int pid = find_problem(tile_start, nprob, blockIdx.x);
-  const OzPackDesc& p = descs[pid];
-  if (p.active && __ldg(p.active) == 0) return;
+// rows of the packed matrix written along the inner index, two columns per
+// thread when k is even), or, for the tiles past the data, the zero padding
+// of every slice.
+template <int S>
+__device__ __forceinline__ void pack_tile(const OzPackDesc& p, int t, z64 (&tile)[32][33], int (&ex)[32]) {
   const int nvec = p.role == 0 ? p.rows : p.rows / 2;
   const int k = p.k;
   const int kt = (k + 31) / 32, pt = (p.w - 2 * k + 31) / 32;
-  const int t = blockIdx.x - __ldg(tile_start + pid);
   const int v0 = (t / (kt + pt)) * 32, ti = t % (kt + pt);
   const int nrow_per_vec = p.role == 0 ? 1 : 2;
-  const size_t rowlen = (size_t)p.S * p.w;
+  const size_t rowlen = (size_t)S * p.w;
   if (ti >= kt) {  // zero padding columns [2k + 32 (ti - kt), ...)
     const int c0 = 2 * k + 32 * (ti - kt);
     for (int e = threadIdx.x; e < 32 * 32 * nrow_per_vec; e += 256) {
@@ -376,13 +397,12 @@ __global__ void __launch_bounds__(256) oz_pack_kernel(const OzPackDesc* __restri
       const int v = v0 + vr / nrow_per_vec;
       if (v >= nvec || c >= p.w) continue;
       const int row = p.role == 0 ? v : 2 * v + (vr % 2);
-      for (int s = 0; s < p.S; ++s) p.out[(size_t)row * rowlen + (size_t)s * p.w + c] = __double2bfloat16(0.0);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) p.out[(size_t)row * rowlen + (size_t)s2 * p.w + c] = __double2bfloat16(0.0);
     }
     return;
   }
   const int k0 = ti * 32;
-  __shared__ z64 tile[32][33];
-  __shared__ int ex[32];
   const bool ci = contig_inner(p);
   for (int e = threadIdx.x; e < 1024; e += 256) {
     const int a = e / 32, b = e % 32;
@@ -392,23 +412,63 @@ __global__ void __launch_bounds__(256) oz_pack_kernel(const OzPackDesc* __restri
   }
   if (threadIdx.x < 32) ex[threadIdx.x] = v0 + threadIdx.x < nvec ? exp_of(p.maxb[v0 + threadIdx.x]) : 0;
   __syncthreads();
+  const int beta = p.beta_bits;
+  if ((k & 1) == 0) {
+    for (int e = threadIdx.x; e < 512; e += 256) {
+      const int vv = e / 16, kk = 2 * (e % 16);
+      const int v = v0 + vv, kg = k0 + kk;
+      if (v >= nvec || kg >= k) continue;  // k even: kg + 1 < k as well
+      const z64 z0 = tile[vv][kk], z1 = tile[vv][kk + 1];
+      if (p.role == 0) {  // A' row v = [Ar | Ai]
+        __nv_bfloat16* row = p.out + (size_t)v * rowlen;
+        write_digits2<S>(row, p.w, kg, beta, z0.x, z1.x, ex[vv]);
+        write_digits2<S>(row, p.w, k + kg, beta, z0.y, z1.y, ex[vv]);
+      } else {  // B' rows 2v = [Br | -Bi], 2v+1 = [Bi | Br]
+        __nv_bfloat16* r0 = p.out + (size_t)(2 * v) * rowlen;
+        __nv_bfloat16* r1 = r0 + rowlen;
+        write_digits2<S>(r0, p.w, kg, beta, z0.x, z1.x, ex[vv]);
+        write_digits2<S>(r0, p.w, k + kg, beta, -z0.y, -z1.y, ex[vv]);
+        write_digits2<S>(r1, p.w, kg, beta, z0.y, z1.y, ex[vv]);
+        write_digits2<S>(r1, p.w, k + kg, beta, z0.x, z1.x, ex[vv]);
+      }
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < 1024; e += 256) {
     const int vv = e / 32, kk = e % 32;
     const int v = v0 + vv, kg = k0 + kk;
     if (v >= nvec || kg >= k) continue;
     const z64 z = tile[vv][kk];
-    if (p.role == 0) {  // A' row v = [Ar | Ai]
+    if (p.role == 0) {
       __nv_bfloat16* row = p.out + (size_t)v * rowlen;
-      write_digits(row, p.w, kg, p.S, p.beta_bits, z.x, ex[vv]);
-      write_digits(row, p.w, k + kg, p.S, p.beta_bits, z.y, ex[vv]);
-    } else {  // B' rows 2v = [Br | -Bi], 2v+1 = [Bi | Br]
+      write_digits1<S>(row, p.w, kg, beta, z.x, ex[vv]);
+      write_digits1<S>(row, p.w, k + kg, beta, z.y, ex[vv]);
+    } else {
       __nv_bfloat16* r0 = p.out + (size_t)(2 * v) * rowlen;
       __nv_bfloat16* r1 = r0 + rowlen;
-      write_digits(r0, p.w, kg, p.S, p.beta_bits, z.x, ex[vv]);
-      write_digits(r0, p.w, k + kg, p.S, p.beta_bits, -z.y, ex[vv]);
-      write_digits(r1, p.w, kg, p.S, p.beta_bits, z.y, ex[vv]);
-      write_digits(r1, p.w, k + kg, p.S, p.beta_bits, z.x, ex[vv]);
+      write_digits1<S>(r0, p.w, kg, beta, z.x, ex[vv]);
+      write_digits1<S>(r0, p.w, k + kg, beta, -z.y, ex[vv]);
+      write_digits1<S>(r1, p.w, kg, beta, z.y, ex[vv]);
+      write_digits1<S>(r1, p.w, k + kg, beta, z.x, ex[vv]);
     }
+  }
+}
+
+__global__ void __launch_bounds__(256, 3) oz_pack_kernel(const OzPackDesc* __restrict__ descs,
+                                                      const int* __restrict__ tile_start, int nprob) {
+  const int pid = find_problem(tile_start, nprob, blockIdx.x);
+  const OzPackDesc& p = descs[pid];
+  if (p.active && __ldg(p.active) == 0) return;
+  __shared__ z64 tile[32][33];
+  __shared__ int ex[32];
+  const int t = blockIdx.x - __ldg(tile_start + pid);
+  switch (p.S) {  // the slice counts oz_plan produces (beta 7 .. 3)
+    case 8: pack_tile<8>(p, t, tile, ex); break;
+    case 9: pack_tile<9>(p, t, tile, ex); break;
+    case 11: pack_tile<11>(p, t, tile, ex); break;
+    case 14: pack_tile<14>(p, t, tile, ex); break;
+    case 18: pack_tile<18>(p, t, tile, ex); break;
+    default: break;
   }
 }
 
@@ -441,7 +501,7 @@ void oz_plan(int k, OzShape* sh) {
     if (lim <= 1.0) continue;  // not even one pair fits an exact pass
     const int npmax = (int)((16777215.0 / (double)(1 << (2 * beta))) / (double)w);
     if (npmax < 1) continue;
-    const int S = (54 + beta - 1) / beta;
+    const int S = (54 + beta - 1) / beta;  // 8, 9, 11, 14, 18: the instances of the packing kernel
     int npass = 0;
     for (int lev = 0; lev < S; ++lev) npass += (lev + 1 + npmax - 1) / npmax;
     if (npass > OZ_MAXPASS) continue;
