@@ -130,18 +130,19 @@ def oracle_point(dev, E, inj):
 
 
 def cpu_baseline(devs, pts, inj, budget_s=30.0):
-    """Oracle (RGF + doubling, FP64 numpy on the host cores) on a bounded sample."""
+    """Oracle (RGF + doubling, FP64 numpy on the host cores) on a bounded sample;
+    also returns the oracle's T of the sampled points."""
     t0 = time.perf_counter()
-    done = 0
+    Ts = []
     for (E, k) in pts:
-        oracle_point(devs[k], E, inj)
-        done += 1
+        Ts.append(float(oracle_point(devs[k], E, inj)["T"]))
         if time.perf_counter() - t0 > budget_s * 0.5:
             break
     dt = time.perf_counter() - t0
+    done = len(Ts)
     return {"value": done / dt, "unit": "(E,k) solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{done} (E,k) point(s) of the workload, FP64 numpy RGF + Sancho-Rubio doubling, "
-                      f"{dt:.1f} s"}
+            "sample": f"{done} (E,k) point(s) of the workload (the first timed ones), FP64 numpy RGF + "
+                      f"Sancho-Rubio doubling, {dt:.1f} s"}, Ts
 
 
 def run_reference(a):
@@ -366,9 +367,16 @@ def main():
                "d2h_bytes_per_step": P * a.n_b * a.s_b * a.n_inj * 16 + P * 8}
 
     if rank == 0:
-        cpu = None
+        cpu, vs_oracle = None, None
         if not a.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline(devs, pts, inj_host[0])
+            first = [mine[(a.warmup * P + i) % len(mine)] for i in range(len(mine))]
+            cpu, T_or = cpu_baseline(devs, first, inj_host[0])
+            n_or = len(T_or)
+            rel = lambda T: max(abs(x - y) / max(1.0, abs(y)) for x, y in zip(T[:n_or], T_or))
+            vs_oracle = {"points": n_or, "max_rel_T_err_" + ("fp64" if head_prec == ss.SS_FP64 else "mixed"):
+                         rel(head["T"])}
+            if other is not None:
+                vs_oracle["max_rel_T_err_fp64"] = rel(other["T"])
         cmp = None
         if other is not None:
             nT = len(other["T"])
@@ -394,6 +402,7 @@ def main():
             "kernels_launches": {k: v["launches"] for k, v in kern.items() if v["launches"]},
             "mixed_vs_fp64": cmp,
             "cpu_baseline": cpu,
+            "T_vs_oracle": vs_oracle,
             "e2e": e2e,
             "gpu_launches": head["launches"],
             "clocks": clk.summary(),

@@ -260,16 +260,22 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) lu_panel_reg_kernel(const Lu
 // updates its own rows.  The published slots alternate between two buffers,
 // so a slot is rewritten only after every CTA has passed the next barrier.
 // Same arithmetic, in the same order, as the single-CTA kernels.
-template <int NB>
+template <int NB, int CL>
 struct ClusterPanelShared {
+  // published for the other CTAs of the cluster (two buffers)
   double cval[2];
   int cidx[2], cbad[2];
   z64 cand_row[2][NB];
   z64 diag_row[2][NB];
-  z64 prow[NB], crow[NB];
+  // this CTA's copies of every CTA's candidate and of the diagonal row
+  double rval[CL];
+  int ridx[CL], rbad[CL];
+  z64 rrow[CL][NB];
+  z64 crow[NB];
   double wv[4];
   int wi[4], wb[4];
-  int piv;
+  int piv, win;
+  z64 inv;
 };
 
 template <int NB, int CL, int NT>
@@ -279,7 +285,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluste
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const LuDesc d = descs[blockIdx.x / CL];
-  __shared__ ClusterPanelShared<NB> sh;
+  __shared__ ClusterPanelShared<NB, CL> sh;
   const bool live = !(d.active && __ldg(d.active) == 0) && k0 < d.s;  // same for the whole cluster
   if (live) {
     const int s = d.s;
@@ -331,60 +337,79 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluste
           for (int c = 0; c < NB; ++c) sh.diag_row[buf][c] = a[c];
         }
         cluster.sync();
-        // global pivot from the CL candidates (every CTA computes the same)
-        if (warp == 0) {
-          double bv = -1.0;
-          int bix = s, anyb = 0;
-          if (lane < CL) {
-            const ClusterPanelShared<NB>* o = cluster.map_shared_rank(&sh, lane);
-            bv = o->cval[buf]; bix = o->cidx[buf]; anyb = o->cbad[buf];
-          }
-          anyb = __any_sync(0xffffffffu, anyb);
+        // one round of distributed shared memory reads: every CTA's candidate
+        // (modulus, row index, values) and the diagonal row
+        {
+          constexpr int NR = CL * (NB + 1) + NB, NI = (NR + NT - 1) / NT;
+          const int cc = (col - k0) % CL;
+          z64 vals[NI];
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-            const int oi = __shfl_down_sync(0xffffffffu, bix, off);
-            if (ov > bv || (ov == bv && oi < bix)) { bv = ov; bix = oi; }
+          for (int i = 0; i < NI; ++i) {
+            const int e = tid + i * NT;
+            vals[i] = zmk(0.0, 0.0);
+            if (e < CL) {
+              const ClusterPanelShared<NB, CL>* o = cluster.map_shared_rank(&sh, e);
+              vals[i] = zmk(o->cval[buf], __hiloint2double(o->cbad[buf], o->cidx[buf]));
+            } else if (e < CL + CL * NB) {
+              const int q = (e - CL) / NB, c = (e - CL) % NB;
+              vals[i] = cluster.map_shared_rank(&sh, q)->cand_row[buf][c];
+            } else if (e < NR) {
+              vals[i] = cluster.map_shared_rank(&sh, cc)->diag_row[buf][e - CL - CL * NB];
+            }
           }
-          bv = __shfl_sync(0xffffffffu, bv, 0);
-          bix = __shfl_sync(0xffffffffu, bix, 0);
-          const bool badp = anyb || !(bv > 0.0) || !isfinite(bv) || bix >= s;
-          if (bix >= s) bix = col;
-          const int cp = (bix - k0) % CL, cc = (col - k0) % CL;
-          if (lane < NB) {
-            const ClusterPanelShared<NB>* op = cluster.map_shared_rank(&sh, cp);
-            const ClusterPanelShared<NB>* oc = cluster.map_shared_rank(&sh, cc);
-            // the winner's published candidate row is the pivot row (its own
-            // diagonal row when the pivot column has no usable entry)
-            sh.prow[lane] = (bix == col) ? oc->diag_row[buf][lane] : op->cand_row[buf][lane];
-            sh.crow[lane] = oc->diag_row[buf][lane];
-          }
-          if (lane == 0) {
-            sh.piv = bix;
-            if (crank == 0) {
-              if (badp && d.info && *d.info == 0) *d.info = col + 1;
-              d.ipiv[col] = bix;
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+            const int e = tid + i * NT;
+            if (e < CL) {
+              sh.rval[e] = vals[i].x;
+              sh.ridx[e] = __double2loint(vals[i].y);
+              sh.rbad[e] = __double2hiint(vals[i].y);
+            } else if (e < CL + CL * NB) {
+              sh.rrow[(e - CL) / NB][(e - CL) % NB] = vals[i];
+            } else if (e < NR) {
+              sh.crow[e - CL - CL * NB] = vals[i];
             }
           }
         }
         __syncthreads();
+        // global pivot (largest modulus, lowest row on ties), its reciprocal
+        if (tid == 0) {
+          double bv = sh.rval[0];
+          int bix = sh.ridx[0], anyb = sh.rbad[0], win = 0;
+          for (int q = 1; q < CL; ++q) {
+            if (sh.rval[q] > bv || (sh.rval[q] == bv && sh.ridx[q] < bix)) { bv = sh.rval[q]; bix = sh.ridx[q]; win = q; }
+            anyb |= sh.rbad[q];
+          }
+          const bool badp = anyb || !(bv > 0.0) || !isfinite(bv) || bix >= s;
+          if (bix >= s) bix = col;
+          // the winner's published candidate row is the pivot row (the
+          // diagonal row itself when it wins or the column has no usable entry)
+          sh.piv = bix;
+          sh.win = (bix == col) ? -1 : win;
+          sh.inv = zinv(bix == col ? sh.crow[J] : sh.rrow[win][J]);
+          if (crank == 0) {
+            if (badp && d.info && *d.info == 0) *d.info = col + 1;
+            d.ipiv[col] = bix;
+          }
+        }
+        __syncthreads();
+        const z64* prow = sh.win < 0 ? sh.crow : sh.rrow[sh.win];
         const int p = sh.piv;
         if (p != col) {
           if (row == col) {
 #pragma unroll
-            for (int c = 0; c < NB; ++c) a[c] = sh.prow[c];
+            for (int c = 0; c < NB; ++c) a[c] = prow[c];
           } else if (row == p) {
 #pragma unroll
             for (int c = 0; c < NB; ++c) a[c] = sh.crow[c];
           }
         }
         if (row > col && row < s) {
-          const z64 inv = zinv(sh.prow[J]);
-          const z64 l = zmul(a[J], inv);
+          const z64 l = zmul(a[J], sh.inv);
           a[J] = l;
 #pragma unroll
           for (int c = J + 1; c < NB; ++c) {
-            const z64 u = sh.prow[c];
+            const z64 u = prow[c];
             a[c].x = fma(-l.x, u.x, a[c].x);
             a[c].x = fma(l.y, u.y, a[c].x);
             a[c].y = fma(-l.x, u.y, a[c].y);
@@ -402,7 +427,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluste
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-constexpr int RB_THREADS = 128;
+constexpr int RB_THREADS = 64;  // one thread per column; small CTAs spread the FP64 work over more SMs
 
 // Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
 // columns to its right (right-hand sides included).  With an outer block

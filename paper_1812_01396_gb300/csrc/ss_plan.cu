@@ -71,10 +71,10 @@ bool Plan::oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, s
                          bool lu_label) {
   std::map<OpKey, int> index;
   std::vector<OzPackDesc> pk;
-  std::vector<CUtensorMap> maps;
+  std::vector<size_t> dbytes;  // digit bytes of each distinct operand
   std::vector<int> amap(ds.size()), bmap(ds.size());
   std::vector<OzShape> shapes(ds.size());
-  size_t used = 0;
+  size_t nmax = 0;  // maxima of all operands, one contiguous array
   for (size_t i = 0; i < ds.size(); ++i) {
     const GemmDesc& g = ds[i];
     oz_plan(g.k, &shapes[i]);
@@ -88,23 +88,15 @@ bool Plan::oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, s
       auto it = index.find(key);
       int mi;
       if (it == index.end()) {
-        const size_t bytes = al1k((size_t)rows * sh.S * sh.w * 2);
-        const size_t ebytes = al1k((size_t)vecs * sizeof(unsigned long long));
-        if (used + bytes + ebytes > cap) return false;
         OzPackDesc d{};
         d.x = o.p; d.s = o.s; d.e = o.e; d.ld = o.ld; d.trans = o.trans; d.role = role;
         d.rows = rows; d.k = g.k; d.w = sh.w; d.S = sh.S; d.beta_bits = sh.beta;
-        d.out = reinterpret_cast<__nv_bfloat16*>(pack + used);
-        d.maxb = reinterpret_cast<unsigned long long*>(pack + used + bytes);
+        d.maxb = reinterpret_cast<unsigned long long*>(pack) + nmax;
         d.active = g.active;
-        CUtensorMap m;
-        if (encode_kmajor_map(&m, pack + used, rows, sh.S * sh.w, role == 0 ? oz_box_rows_a() : oz_box_rows_b()) !=
-            cudaSuccess)
-          return false;
-        used += bytes + ebytes;
-        mi = (int)maps.size();
-        maps.push_back(m);
+        nmax += (size_t)vecs;
+        mi = (int)pk.size();
         pk.push_back(d);
+        dbytes.push_back(al1k((size_t)rows * sh.S * sh.w * 2));
         index[key] = mi;
       } else {
         mi = it->second;
@@ -112,12 +104,20 @@ bool Plan::oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, s
       (role == 0 ? amap : bmap)[i] = mi;
     }
   }
-  // maxima (zeroed first), then digit slices
+  // layout: [maxima | digit slices of each operand, 1 KB aligned]
+  size_t used = al1k(nmax * sizeof(unsigned long long));
+  std::vector<CUtensorMap> maps(pk.size());
+  for (size_t q = 0; q < pk.size(); ++q) {
+    if (used + dbytes[q] > cap) return false;
+    pk[q].out = reinterpret_cast<__nv_bfloat16*>(pack + used);
+    if (encode_kmajor_map(&maps[q], pack + used, pk[q].rows, pk[q].S * pk[q].w,
+                          pk[q].role == 0 ? oz_box_rows_a() : oz_box_rows_b()) != cudaSuccess)
+      return false;
+    used += dbytes[q];
+  }
+  // maxima (zeroed first, one memset for the group), then digit slices
   {
-    for (auto& d : pk) {
-      const int nvec = d.role == 0 ? d.rows : d.rows / 2;
-      memset0(d.maxb, (size_t)nvec * sizeof(unsigned long long));
-    }
+    memset0(pack, nmax * sizeof(unsigned long long));
     std::vector<int> start(pk.size());
     int tot = 0;
     for (size_t i = 0; i < pk.size(); ++i) {
