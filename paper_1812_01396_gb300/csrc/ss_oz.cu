@@ -19,12 +19,17 @@
 //     up to np pairs of one level are accumulated in one FP32 TMEM
 //     accumulator, with np * w * 2^{2 beta} < 2^24 so that every partial sum
 //     is an integer below 2^24 and the FP32 accumulation is EXACT;
-//   * each such accumulation ("pass") is drained by the epilogue into FP64
-//     registers, scaled by 2^{eA[i] + eB[j] - beta (d+2)}; four TMEM
-//     accumulators form a ring so the MMA thread runs ahead of the epilogue.
+//   * each such accumulation ("pass") is drained by the epilogue into an
+//     int64 fixed point, scaled by 2^{eA[i] + eB[j] - beta (d+2)} at the end;
+//     four TMEM accumulators form a ring so the MMA thread runs ahead of the
+//     epilogue.
 //
-// Levels d <= S - 1 are kept (the dropped ones are below 2^-54 of the
-// largest product), so the result matches an FP64 GEMM to rounding.
+// The digits cover OZ_DIGIT_BITS = 60 bits below each row / column maximum:
+// 54 would resolve the largest entries to FP64 precision, the 6 extra keep
+// entries up to 64 times smaller than their row maximum at FP64 precision
+// too (products pairing a small entry of A with a large one of B otherwise
+// lose those bits; on the doubling of the leads this tripled the error of T).
+// Levels d <= S - 1 are kept, so the result matches an FP64 GEMM to rounding.
 // Persistent CTAs over 128 x 128 tiles of C' = A' B'^T; warp 0 issues TMA,
 // warp 1 the MMAs, warps 2-9 drain the accumulators.  Every wait is bounded
 // (2 s).
@@ -41,6 +46,7 @@ namespace ss {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6, NACC = 4;
+constexpr int OZ_DIGIT_BITS = 60;  // bits below the row / column maximum the digits cover
 // Tiles of a problem are visited in groups of GM row tiles (column-major
 // inside a group), so the CTAs running at the same time share A row panels
 // and B column panels and their digit slices stay in L2.
@@ -463,11 +469,11 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const OzPackDesc* __res
   __shared__ int ex[32];
   const int t = blockIdx.x - __ldg(tile_start + pid);
   switch (p.S) {  // the slice counts oz_plan produces (beta 7 .. 3)
-    case 8: pack_tile<8>(p, t, tile, ex); break;
     case 9: pack_tile<9>(p, t, tile, ex); break;
-    case 11: pack_tile<11>(p, t, tile, ex); break;
-    case 14: pack_tile<14>(p, t, tile, ex); break;
-    case 18: pack_tile<18>(p, t, tile, ex); break;
+    case 10: pack_tile<10>(p, t, tile, ex); break;
+    case 12: pack_tile<12>(p, t, tile, ex); break;
+    case 15: pack_tile<15>(p, t, tile, ex); break;
+    case 20: pack_tile<20>(p, t, tile, ex); break;
     default: break;
   }
 }
@@ -487,7 +493,7 @@ int oz_pack_tiles(const OzPackDesc& d) {
 int oz_box_rows_a() { return BM; }
 int oz_box_rows_b() { return BN; }
 
-// Choose beta (bits per digit) for slices of width w: S = ceil(54 / beta)
+// Choose beta (bits per digit) for slices of width w: S = ceil(60 / beta)
 // slices; at most npmax digit pairs of one level share an exact FP32 pass
 // (npmax * w * 2^{2 beta} < 2^24).  Cost = tensor K-tiles (pairs * w / 64)
 // plus about four K-tiles per pass drained by the epilogue; the cheapest
@@ -501,7 +507,7 @@ void oz_plan(int k, OzShape* sh) {
     if (lim <= 1.0) continue;  // not even one pair fits an exact pass
     const int npmax = (int)((16777215.0 / (double)(1 << (2 * beta))) / (double)w);
     if (npmax < 1) continue;
-    const int S = (54 + beta - 1) / beta;  // 8, 9, 11, 14, 18: the instances of the packing kernel
+    const int S = (OZ_DIGIT_BITS + beta - 1) / beta;  // 9, 10, 12, 15, 20: the packing kernel's instances
     int npass = 0;
     for (int lev = 0; lev < S; ++lev) npass += (lev + 1 + npmax - 1) / npmax;
     if (npass > OZ_MAXPASS) continue;
