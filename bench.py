@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="eager launches (for profiler runs)")
+    ap.add_argument("--gemm", default=None, metavar="MxNxK",
+                    help="time one complex GEMM through ss_zgemm (exact tensor-core and FP64 kernels) "
+                         "instead of the pipeline; prints its own JSON line")
     return ap.parse_args()
 
 
@@ -190,10 +193,42 @@ def fp64_gemm_peak(torch):
     return best
 
 
+def run_gemm(a):
+    """One C = A B (complex128, random N(0,1) entries) through ss_zgemm: the exact
+    digit-sliced tensor-core kernel and the FP64 kernel, each call including its
+    packing, timed with CUDA events after warm-up; error vs cuBLAS ZGEMM."""
+    import torch
+
+    import paper_1812_01396_gb300 as ss
+    m, n, k = (int(v) for v in a.gemm.lower().split("x"))
+    torch.manual_seed(0)
+    A = torch.randn(m, k, dtype=torch.complex128, device="cuda")
+    B = torch.randn(k, n, dtype=torch.complex128, device="cuda")
+    C = torch.empty(m, n, dtype=torch.complex128, device="cuda")
+    ref = A @ B
+    out = {"gemm": [m, n, k], "unit": "ms per call", "flops_fp64_equiv": 8.0 * m * n * k}
+    for name, prec in (("exact_tc", ss.SS_MIXED_OZAKI), ("fp64", ss.SS_FP64)):
+        for _ in range(max(a.warmup, 1)):
+            ss.ss_zgemm(A, B, C, precision=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.steps):
+            ss.ss_zgemm(A, B, C, precision=prec)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        out[name] = {"ms": ms, "tflops_fp64_equiv": out["flops_fp64_equiv"] / ms / 1e9,
+                     "max_rel_err_vs_cublas": float((C - ref).abs().max() / ref.abs().max())}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.gemm:
+        return run_gemm(a)
     import torch
     import torch.distributed as dist
 
