@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="eager launches (for profiler runs)")
+    ap.add_argument("--workload", default="nanowire", choices=["nanowire", "uneven", "dense"],
+                    help="nanowire: the bench line (default); uneven: 256 points over 8 devices of "
+                         "s_b in {256,384,512}, n_b in {32,64,128}, batched vs one point per call; dense: "
+                         "dense random blocks (default n_b 48, s_b 2048), mixed vs FP64 vs oracle on few "
+                         "points.  uneven and dense print their own JSON line")
+    ap.add_argument("--points", type=int, default=2, help="dense workload: points of the mixed path")
     ap.add_argument("--gemm", default=None, metavar="MxNxK",
                     help="time one complex GEMM through ss_zgemm (exact tensor-core and FP64 kernels) "
                          "instead of the pipeline; prints its own JSON line")
@@ -223,12 +229,90 @@ def run_gemm(a):
     print(json.dumps(out), flush=True)
 
 
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def run_uneven(a):
+    """256 (E,k) points over 8 devices of uneven (s_b, n_b) (seeded), mixed path:
+    one batched call (grouped launches, CUDA graphs, autotuned LU, chunks of
+    8 points) against one call per point on the same handle."""
+    import paper_1812_01396_gb300 as ss
+    shapes = synth.uneven_points(8, seed=3)
+    rng = np.random.default_rng(3)
+    h = ss.Handle(n_b_max=128, s_b_max=512, max_points=8, max_inj=1, precision=ss.SS_MIXED_OZAKI)
+    E, kid = [], []
+    for d, (s_b, n_b, _, _) in enumerate(shapes):
+        # one k of the nanowire set per device keeps the 8 devices' blocks near 17 GB
+        dev = synth.make_device(n_b, s_b, seed=30 + d, band=s_b // 20, s_pert=0.02,
+                                k_points=(synth.K_POINTS_4[d % 4],), w_scale=0.25)[0]
+        h.set_device(d, dev)
+        for _ in range(32):
+            E.append(float(rng.uniform(-1.0, 1.0)))
+            kid.append(d)
+    for s_b in sorted({sh[0] for sh in shapes}):
+        h.autotune(s_b, 16, os.path.join(tempfile.gettempdir(), "splitsolve_autotune.txt"))
+    h.transmission(E[:8], kid[:8])  # warm-up
+    (Tb, _, stb, _), tb = _timed(lambda: h.transmission(E, kid))
+    Tp, sp = np.zeros(len(E)), np.zeros(len(E), np.int32)
+
+    def per_point():
+        for i in range(len(E)):
+            T, _, st, _ = h.transmission([E[i]], [kid[i]])
+            Tp[i], sp[i] = T[0], st[0]
+    _, tp = _timed(per_point)
+    h.close()
+    diff = float(np.max(np.abs(np.asarray(Tb) - Tp) / np.maximum(1.0, np.abs(Tp))))
+    print(json.dumps({"workload": "uneven: 256 (E,k) points over 8 devices " + str([sh[:2] for sh in shapes]) +
+                      " (s_b, n_b), mixed path", "unit": "(E,k) solves/s",
+                      "batched": len(E) / tb, "per_point_calls": len(E) / tp, "speedup": tp / tb,
+                      "max_rel_T_diff_batched_vs_per_point": diff,
+                      "status_ok": bool(np.all(np.asarray(stb) == 0) and np.all(sp == 0))}), flush=True)
+
+
+def run_dense(a):
+    """Dense random blocks (n_b 48, s_b 2048 unless given): the mixed path on
+    --points points, the FP64 path and the oracle on the first one."""
+    import paper_1812_01396_gb300 as ss
+    n_b = a.n_b if a.n_b != 64 else 48
+    s_b = a.s_b if a.s_b != 512 else 2048
+    dev = synth.make_device(n_b, s_b, seed=4, s_pert=0.05)[0]
+    Es = [float(e) for e in synth.energy_grid(32)][:a.points]
+    out = {"workload": f"dense random blocks, n_b={n_b}, s_b={s_b}, k=0, energies of a 32-point grid on [-1,1]",
+           "unit": "s per (E,k) point"}
+    Ts = {}
+    for name, prec, pts in (("mixed", ss.SS_MIXED_OZAKI, Es), ("fp64", ss.SS_FP64, Es[:1])):
+        h = ss.Handle(n_b_max=n_b, s_b_max=s_b, max_points=len(pts), max_inj=1, precision=prec)
+        h.set_device(0, dev)
+        (T, err, st, _), t = _timed(lambda: h.transmission(pts, [0] * len(pts)))
+        h.close()
+        Ts[name] = np.asarray(T)
+        out[name] = {"points": len(pts), "s_per_point": t / len(pts), "status": [int(v) for v in st],
+                     "err_est": [float(v) for v in err]}
+    out["rel_T_mixed_vs_fp64"] = float(abs(Ts["mixed"][0] - Ts["fp64"][0]) / max(1.0, abs(Ts["fp64"][0])))
+    if not a.no_cpu_baseline:
+        t0 = time.perf_counter()
+        T_or = float(oracle_point(dev, Es[0], None)["T"])
+        out["oracle"] = {"s_per_point": time.perf_counter() - t0, "cores": os.cpu_count()}
+        out["rel_T_vs_oracle"] = {k: float(abs(v[0] - T_or) / max(1.0, abs(T_or))) for k, v in Ts.items()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.gemm:
         return run_gemm(a)
+    if a.workload == "uneven":
+        return run_uneven(a)
+    if a.workload == "dense":
+        return run_dense(a)
     import torch
     import torch.distributed as dist
 
