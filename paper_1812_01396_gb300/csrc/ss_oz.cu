@@ -10,15 +10,16 @@
 //     scale 2^eA[i] >= its largest |entry|, every column j of op(B) a scale
 //     2^eB[j] (shared by the re and im rows 2j, 2j+1 of B');
 //   * each scaled value r in (-1, 1) is cut into S integer digits of beta bits,
-//     r = sum_t d_t 2^{-beta (t+1)}, |d_t| <= 2^beta: every digit is an exact
-//     BF16 number;
+//     r = sum_t d_t 2^{-beta (t+1)}, |d_0| <= 2^beta, |d_t| <= 2^(beta-1) for
+//     t > 0 (round to nearest): every digit is an exact BF16 number;
 //   * A' = [A_0 | A_1 | ... | A_{S-1}] and B' likewise (each slice w >= 2k
 //     wide, zero padded), so the product of digit slices t and u is a plain
 //     K-major BF16 GEMM;
 //   * slices with the same level d = t + u share the scale 2^{-beta (d+2)};
-//     up to np pairs of one level are accumulated in one FP32 TMEM
-//     accumulator, with np * w * 2^{2 beta} < 2^24 so that every partial sum
-//     is an integer below 2^24 and the FP32 accumulation is EXACT;
+//     consecutive pairs of one level share one FP32 TMEM accumulator while
+//     the sum of their bounds w |d_t| |d_u| stays <= 2^24, so that every
+//     partial sum is an integer of at most 24 bits and the FP32 accumulation
+//     is EXACT;
 //   * each such accumulation ("pass") is drained by the epilogue into an
 //     int64 fixed point, scaled by 2^{eA[i] + eB[j] - beta (d+2)} at the end;
 //     four TMEM accumulators form a ring so the MMA thread runs ahead of the
@@ -468,7 +469,8 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const OzPackDesc* __res
   __shared__ z64 tile[32][33];
   __shared__ int ex[32];
   const int t = blockIdx.x - __ldg(tile_start + pid);
-  switch (p.S) {  // the slice counts oz_plan produces (beta 7 .. 3)
+  switch (p.S) {  // the slice counts oz_plan produces (beta 8 .. 3)
+    case 8: pack_tile<8>(p, t, tile, ex); break;
     case 9: pack_tile<9>(p, t, tile, ex); break;
     case 10: pack_tile<10>(p, t, tile, ex); break;
     case 12: pack_tile<12>(p, t, tile, ex); break;
@@ -494,25 +496,51 @@ int oz_box_rows_a() { return BM; }
 int oz_box_rows_b() { return BN; }
 
 // Choose beta (bits per digit) for slices of width w: S = ceil(60 / beta)
-// slices; at most npmax digit pairs of one level share an exact FP32 pass
-// (npmax * w * 2^{2 beta} < 2^24).  Cost = tensor K-tiles (pairs * w / 64)
-// plus about four K-tiles per pass drained by the epilogue; the cheapest
-// beta with at most OZ_MAXPASS passes wins.
+// slices.  Digit bounds: the leading digit of a value is at most 2^beta in
+// magnitude, every later digit at most 2^(beta-1) (round to nearest leaves a
+// remainder of at most half a unit), so a digit pair (t, u) contributes at
+// most w * 2^(2 beta - [t>0] - [u>0]) to a pass.  The pairs of one level are
+// packed into passes greedily while that sum stays <= 2^24 (every partial sum
+// then an integer an FP32 accumulator holds exactly).  Cost = tensor K-tiles
+// (pairs * w / 64) plus about four K-tiles per pass drained by the epilogue;
+// the cheapest beta with at most OZ_MAXPASS passes wins.  beta <= 8 keeps every
+// digit (|d| <= 256) an exact BF16 number.
+namespace {
+int oz_passes(int w, int beta, int S, OzShape* out) {
+  const double cap = 16777216.0;
+  int n = 0;
+  for (int lev = 0; lev < S; ++lev) {
+    int t0 = 0;
+    double acc = 0.0;
+    for (int t = 0; t <= lev; ++t) {
+      const int e = 2 * beta - (t > 0) - (lev - t > 0);
+      const double b = (double)w * (double)(1ll << e);
+      if (b > cap) return OZ_MAXPASS + 1;  // one pair alone is not exact
+      if (acc + b > cap) {                 // close the pass [t0, t)
+        if (out && n < OZ_MAXPASS) { out->pd[n] = (unsigned char)lev; out->pt0[n] = (unsigned char)t0; out->pnp[n] = (unsigned char)(t - t0); }
+        ++n;
+        t0 = t;
+        acc = 0.0;
+      }
+      acc += b;
+    }
+    if (out && n < OZ_MAXPASS) { out->pd[n] = (unsigned char)lev; out->pt0[n] = (unsigned char)t0; out->pnp[n] = (unsigned char)(lev + 1 - t0); }
+    ++n;
+  }
+  return n;
+}
+}  // namespace
+
 void oz_plan(int k, OzShape* sh) {
   const int w = ((2 * k + BK - 1) / BK) * BK;
-  int best_beta = -1, best_S = 0, best_np = 0;
+  int best_beta = -1, best_S = 0;
   double best_cost = 0.0;
-  for (int beta = 7; beta >= 3; --beta) {
-    const double lim = 16777216.0 / ((double)(1 << (2 * beta)) * (double)w);
-    if (lim <= 1.0) continue;  // not even one pair fits an exact pass
-    const int npmax = (int)((16777215.0 / (double)(1 << (2 * beta))) / (double)w);
-    if (npmax < 1) continue;
-    const int S = (OZ_DIGIT_BITS + beta - 1) / beta;  // 9, 10, 12, 15, 20: the packing kernel's instances
-    int npass = 0;
-    for (int lev = 0; lev < S; ++lev) npass += (lev + 1 + npmax - 1) / npmax;
+  for (int beta = 8; beta >= 3; --beta) {
+    const int S = (OZ_DIGIT_BITS + beta - 1) / beta;  // 8, 9, 10, 12, 15, 20: the packing kernel's instances
+    const int npass = oz_passes(w, beta, S, nullptr);
     if (npass > OZ_MAXPASS) continue;
     const double cost = (double)S * (S + 1) / 2 * (w / BK) + 4.0 * npass;
-    if (best_beta < 0 || cost < best_cost) { best_beta = beta; best_S = S; best_np = npmax; best_cost = cost; }
+    if (best_beta < 0 || cost < best_cost) { best_beta = beta; best_S = S; best_cost = cost; }
   }
   sh->w = w;
   sh->npass = 0;
@@ -524,15 +552,7 @@ void oz_plan(int k, OzShape* sh) {
   }
   sh->beta = best_beta;
   sh->S = best_S;
-  for (int lev = 0; lev < best_S; ++lev) {
-    for (int t0 = 0; t0 < lev + 1; t0 += best_np) {
-      const int np = (lev + 1 - t0) < best_np ? (lev + 1 - t0) : best_np;
-      sh->pd[sh->npass] = (unsigned char)lev;
-      sh->pt0[sh->npass] = (unsigned char)t0;
-      sh->pnp[sh->npass] = (unsigned char)np;
-      sh->npass++;
-    }
-  }
+  sh->npass = oz_passes(w, best_beta, best_S, sh);
 }
 
 void launch_oz_scale(const OzPackDesc* d, const int* tile_start, int nprob, int total, cudaStream_t st) {
