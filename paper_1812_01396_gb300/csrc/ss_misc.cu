@@ -36,6 +36,15 @@ __global__ void __launch_bounds__(FNT) zform_kernel(const FormDesc* __restrict__
   const int t = blockIdx.x - __ldg(tile_start + pid);
   const int r0 = (t / tiles_c) * FT, c0 = (t % tiles_c) * FT;
   // each thread handles 4 elements of the 32 x 32 tile
+  const bool copy = d.x && !d.y && !d.z && !d.v && !d.nrm && d.ax.x == 1.0 && d.ax.y == 0.0 &&
+                    d.gamma.x == 0.0 && d.gamma.y == 0.0;
+  if (copy) {  // plain (conjugate-transposed) copy: no FP64 arithmetic, which is slow on this GPU
+    for (int e = threadIdx.x; e < FT * FT; e += FNT) {
+      const int r = r0 + e / FT, c = c0 + e % FT;
+      if (r < d.rows && c < d.cols) d.out[(size_t)r * d.ldo + c] = opget(d.x, d.ldx, d.tx, r, c);
+    }
+    return;
+  }
   double sq = 0.0;
   for (int e = threadIdx.x; e < FT * FT; e += FNT) {
     const int r = r0 + e / FT, c = c0 + e % FT;
