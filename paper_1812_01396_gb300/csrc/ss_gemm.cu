@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
 
   const z64 alpha = d.alpha, beta = d.beta;
   const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+  // C - A B (the LU updates): no complex multiplies in the epilogue
+  const bool sub = d.cmode == 0 && alpha.x == -1.0 && alpha.y == 0.0 && beta.x == 1.0 && beta.y == 0.0;
 #pragma unroll
   for (int i = 0; i < MI; ++i) {
     const int r = row0 + ty + TY * i;
@@ -139,6 +141,13 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
     for (int j = 0; j < MJ; ++j) {
       const int c = col0 + tx + TX * j;
       if (c >= n) continue;
+      if (sub) {
+        const z64 p = Cx<R>::back(acc[i][j]);
+        z64* cp = d.c + (size_t)r * d.ldc + c;
+        const z64 o = *cp;
+        *cp = zmk(o.x - p.x, o.y - p.y);
+        continue;
+      }
       z64 v = zmul(alpha, Cx<R>::back(acc[i][j]));
       if (d.cmode == 1) {
         const size_t fi = (size_t)r * d.ldcf + c;

@@ -318,17 +318,16 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluste
         }
         if (lane == 0) { sh.wv[warp] = best; sh.wi[warp] = bi; sh.wb[warp] = bad; }
         __syncthreads();
-        if (tid == 0) {
-          double bv = sh.wv[0];
-          int bix = sh.wi[0], anyb = sh.wb[0];
-          for (int q = 1; q < NT / 32; ++q) {
-            if (sh.wv[q] > bv || (sh.wv[q] == bv && sh.wi[q] < bix)) { bv = sh.wv[q]; bix = sh.wi[q]; }
-            anyb |= sh.wb[q];
-          }
-          sh.cval[buf] = bv; sh.cidx[buf] = bix; sh.cbad[buf] = anyb;
+        // every thread reduces the warp results, so the CTA's winner knows itself
+        double cbv = sh.wv[0];
+        int cbix = sh.wi[0], canyb = sh.wb[0];
+#pragma unroll
+        for (int q = 1; q < NT / 32; ++q) {
+          if (sh.wv[q] > cbv || (sh.wv[q] == cbv && sh.wi[q] < cbix)) { cbv = sh.wv[q]; cbix = sh.wi[q]; }
+          canyb |= sh.wb[q];
         }
-        __syncthreads();
-        if (row < s && row == sh.cidx[buf]) {
+        if (tid == 0) { sh.cval[buf] = cbv; sh.cidx[buf] = cbix; sh.cbad[buf] = canyb; }
+        if (row < s && row == cbix) {
 #pragma unroll
           for (int c = 0; c < NB; ++c) sh.cand_row[buf][c] = a[c];
         }

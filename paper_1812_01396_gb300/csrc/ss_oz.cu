@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
     // arithmetic is needed only once per output element.
     const int q4 = warp & 3;             // TMEM lanes 32 q4 .. 32 q4 + 31
     const int part = (warp - 2) >> 2;    // real columns EPI_COLS part .. of the tile
-    static_assert(EPI_COLS % 16 == 0, "16-column TMEM loads");
+    static_assert(EPI_COLS % 8 == 0, "8-column TMEM loads");
     int pg = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       int pid, m0, n0;
@@ -219,30 +219,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
         const int sh = 37 - d.beta_bits * d.pd[p];  // shift of this level into the fixed point
         if (ok && !s_fail) {
 #pragma unroll
-          for (int sub = 0; sub < EPI_COLS / 16; ++sub) {
-            uint32_t v[16];
+          for (int sub = 0; sub < EPI_COLS / 8; ++sub) {
+            uint32_t v[8];
             const uint32_t taddr =
-                tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + part * EPI_COLS + sub * 16);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(taddr));
+                tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN + part * EPI_COLS + sub * 8);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (sh >= 0) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                re[sub * 8 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
-                im[sub * 8 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
+              for (int e = 0; e < 4; ++e) {
+                re[sub * 4 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e])) << sh;
+                im[sub * 4 + e] += (long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) << sh;
               }
             } else {
               const int rs = -sh;
               const long long rnd = 1ll << (rs - 1);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                re[sub * 8 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
-                im[sub * 8 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
+              for (int e = 0; e < 4; ++e) {
+                re[sub * 4 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e])) + rnd) >> rs;
+                im[sub * 4 + e] += ((long long)__float2int_rn(__uint_as_float(v[2 * e + 1])) + rnd) >> rs;
               }
             }
           }
