@@ -48,7 +48,10 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, 
 __device__ __forceinline__ z64 op_load(const Operand& o, int i, int j) {
   size_t idx = o.trans ? (size_t)j * o.ld + i : (size_t)i * o.ld + j;
   z64 v = o.p[idx];
-  if (o.s) v = zsub(zmul(o.e, o.s[idx]), v);
+  if (o.s) {  // e S - H; real e (the device at real E) needs two FMAs, not a complex product
+    const z64 sv = o.s[idx];
+    v = o.e.y == 0.0 ? zmk(fma(o.e.x, sv.x, -v.x), fma(o.e.x, sv.y, -v.y)) : zsub(zmul(o.e, sv), v);
+  }
   return o.trans ? zconj(v) : v;
 }
 

@@ -23,6 +23,13 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, 
   return lo;
 }
 
+// y + a x; a real coefficient (the common case) costs two FMAs on the slow
+// FP64 pipe instead of a complex product and an add
+__device__ __forceinline__ z64 zaxpy(z64 a, z64 x, z64 y) {
+  if (a.y == 0.0) return zmk(fma(a.x, x.x, y.x), fma(a.x, x.y, y.y));
+  return zadd(y, zmul(a, x));
+}
+
 __device__ __forceinline__ z64 opget(const z64* p, int ld, int tr, int r, int c) {
   return tr ? zconj(p[(size_t)c * ld + r]) : p[(size_t)r * ld + c];
 }
@@ -50,10 +57,10 @@ __global__ void __launch_bounds__(FNT) zform_kernel(const FormDesc* __restrict__
     const int r = r0 + e / FT, c = c0 + e % FT;
     if (r >= d.rows || c >= d.cols) continue;
     z64 v = (r == c) ? d.gamma : zmk(0.0, 0.0);
-    if (d.x) v = zadd(v, zmul(d.ax, opget(d.x, d.ldx, d.tx, r, c)));
-    if (d.y) v = zadd(v, zmul(d.ay, opget(d.y, d.ldy, d.ty, r, c)));
-    if (d.z) v = zadd(v, zmul(d.az, opget(d.z, d.ldz, d.tz, r, c)));
-    if (d.v) v = zadd(v, zmul(d.av, d.v[(size_t)r * d.ldv + c]));
+    if (d.x) v = zaxpy(d.ax, opget(d.x, d.ldx, d.tx, r, c), v);
+    if (d.y) v = zaxpy(d.ay, opget(d.y, d.ldy, d.ty, r, c), v);
+    if (d.z) v = zaxpy(d.az, opget(d.z, d.ldz, d.tz, r, c), v);
+    if (d.v) v = zaxpy(d.av, d.v[(size_t)r * d.ldv + c], v);
     if (d.nrm) sq = fma(v.x, v.x, fma(v.y, v.y, sq));
     else d.out[(size_t)r * d.ldo + c] = v;
   }

@@ -287,7 +287,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
 __device__ __forceinline__ z64 oz_load(const OzPackDesc& p, int i, int j) {
   const size_t idx = p.trans ? (size_t)j * p.ld + i : (size_t)i * p.ld + j;
   z64 v = p.x[idx];
-  if (p.s) v = zsub(zmul(p.e, p.s[idx]), v);
+  if (p.s) {  // e S - H; real e (the device at real E) needs two FMAs, not a complex product
+    const z64 sv = p.s[idx];
+    v = p.e.y == 0.0 ? zmk(fma(p.e.x, sv.x, -v.x), fma(p.e.x, sv.y, -v.y)) : zsub(zmul(p.e, sv), v);
+  }
   return p.trans ? zconj(v) : v;
 }
 
