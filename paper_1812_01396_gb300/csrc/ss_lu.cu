@@ -433,17 +433,20 @@ constexpr int RB_THREADS = 64;  // one thread per column; small CTAs spread the 
 // width nbo > 0 (two-level blocking) the solve stops at the end of the outer
 // block, K1 = min(K0 + nbo, s): columns from K1 on are swapped now and solved
 // later by the `far` variant, which applies no swaps and solves the rows of
-// this panel on columns K1..ncols-1 only.
+// this panel on columns K1..ncols-1 only.  One thread per column; NB >= nb is
+// the compile-time panel width, and each dot product runs in two halves
+// (even / odd terms) to shorten the dependent FMA chains.
+template <int NB>
 __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* __restrict__ descs,
                                                                  int k0, int nb, int nbo, int far) {
   const LuDesc d = descs[blockIdx.y];
   if (d.active && __ldg(d.active) == 0) return;
   const int s = d.s;
   if (k0 >= s) return;
-  const int nbw = min(nb, s - k0);
+  const int nbw = min(min(nb, NB), s - k0);
   const int K1 = nbo > 0 ? min((k0 / nbo) * nbo + nbo, s) : d.ncols;
-  __shared__ z64 Ls[MAXNB][MAXNB + 1];
-  __shared__ int piv[MAXNB];
+  __shared__ z64 Ls[NB][NB + 1];
+  __shared__ int piv[NB];
   for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
     const int r = e / nbw, c = e % nbw;
     Ls[r][c] = d.w[(size_t)(k0 + r) * d.ldw + k0 + c];
@@ -473,42 +476,43 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
     }
     if (c < k0 || c >= K1) return;
   }
-  z64 x[MAXNB];
+  z64 x[NB];
 #pragma unroll
-  for (int j = 0; j < MAXNB; ++j)
+  for (int j = 0; j < NB; ++j)
     if (j < nbw) x[j] = w[(size_t)(k0 + j) * ld + c];
 #pragma unroll
-  for (int j = 1; j < MAXNB; ++j) {
+  for (int j = 1; j < NB; ++j) {
     if (j < nbw) {
-      z64 acc = x[j];
+      z64 e0 = x[j], e1 = zmk(0.0, 0.0);
 #pragma unroll
-      for (int i = 0; i < MAXNB; ++i)
-        if (i < j) {
-          const z64 l = Ls[j][i];
-          acc.x = fma(-l.x, x[i].x, acc.x);
-          acc.x = fma(l.y, x[i].y, acc.x);
-          acc.y = fma(-l.x, x[i].y, acc.y);
-          acc.y = fma(-l.y, x[i].x, acc.y);
-        }
-      x[j] = acc;
+      for (int i = 0; i < j; ++i) {
+        const z64 l = Ls[j][i];
+        z64& acc = (i & 1) ? e1 : e0;
+        acc.x = fma(-l.x, x[i].x, acc.x);
+        acc.x = fma(l.y, x[i].y, acc.x);
+        acc.y = fma(-l.x, x[i].y, acc.y);
+        acc.y = fma(-l.y, x[i].x, acc.y);
+      }
+      x[j] = zadd(e0, e1);
     }
   }
 #pragma unroll
-  for (int j = 0; j < MAXNB; ++j)
+  for (int j = 0; j < NB; ++j)
     if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
 }
 
 // B_k = U_kk^-1 B_k on the right-hand-side columns (backward substitution
-// within one diagonal block of U).
+// within one diagonal block of U), two FMA chains per dot product as above.
+template <int NB>
 __global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDesc* __restrict__ descs,
                                                                      int k0, int nb) {
   const LuDesc d = descs[blockIdx.y];
   if (d.active && __ldg(d.active) == 0) return;
   const int s = d.s;
   if (k0 >= s) return;
-  const int nbw = min(nb, s - k0);
-  __shared__ z64 Us[MAXNB][MAXNB + 1];
-  __shared__ z64 dinv[MAXNB];
+  const int nbw = min(min(nb, NB), s - k0);
+  __shared__ z64 Us[NB][NB + 1];
+  __shared__ z64 dinv[NB];
   for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
     const int r = e / nbw, c = e % nbw;
     Us[r][c] = d.w[(size_t)(k0 + r) * d.ldw + k0 + c];
@@ -522,28 +526,29 @@ __global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDes
   const int c = s + q;
   z64* __restrict__ w = d.w;
   const size_t ld = d.ldw;
-  z64 x[MAXNB];
+  z64 x[NB];
 #pragma unroll
-  for (int j = 0; j < MAXNB; ++j)
+  for (int j = 0; j < NB; ++j)
     if (j < nbw) x[j] = w[(size_t)(k0 + j) * ld + c];
 #pragma unroll
-  for (int j = MAXNB - 1; j >= 0; --j) {
+  for (int j = NB - 1; j >= 0; --j) {
     if (j < nbw) {
-      z64 acc = x[j];
+      z64 e0 = x[j], e1 = zmk(0.0, 0.0);
 #pragma unroll
-      for (int i = 0; i < MAXNB; ++i)
-        if (i > j && i < nbw) {
+      for (int i = j + 1; i < NB; ++i)
+        if (i < nbw) {
           const z64 u = Us[j][i];
+          z64& acc = (i & 1) ? e1 : e0;
           acc.x = fma(-u.x, x[i].x, acc.x);
           acc.x = fma(u.y, x[i].y, acc.x);
           acc.y = fma(-u.x, x[i].y, acc.y);
           acc.y = fma(-u.y, x[i].x, acc.y);
         }
-      x[j] = zmul(acc, dinv[j]);
+      x[j] = zmul(zadd(e0, e1), dinv[j]);
     }
   }
 #pragma unroll
-  for (int j = 0; j < MAXNB; ++j)
+  for (int j = 0; j < NB; ++j)
     if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
 }
 }  // namespace
@@ -571,13 +576,17 @@ void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int
                         cudaStream_t st) {
   if (nprob <= 0 || max_cols <= 0) return;
   dim3 grid((max_cols + RB_THREADS - 1) / RB_THREADS, nprob);
-  lu_rowblock_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
+  if (nb <= 8) lu_rowblock_kernel<8><<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
+  else if (nb <= 16) lu_rowblock_kernel<16><<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
+  else lu_rowblock_kernel<MAXNB><<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
 }
 
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs, cudaStream_t st) {
   if (nprob <= 0 || max_rhs <= 0) return;
   dim3 grid((max_rhs + RB_THREADS - 1) / RB_THREADS, nprob);
-  lu_backsub_diag_kernel<<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+  if (nb <= 8) lu_backsub_diag_kernel<8><<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+  else if (nb <= 16) lu_backsub_diag_kernel<16><<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
+  else lu_backsub_diag_kernel<MAXNB><<<grid, RB_THREADS, 0, st>>>(d, k0, nb);
 }
 
 }  // namespace ss

@@ -265,6 +265,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzDesc* __
               out = zadd(out, zmul(d.beta, zsub(zmul(d.ce, d.cs[fi]), d.ch[fi])));
             } else if (d.cmode == 2) {
               if (row == j) out = zadd(out, d.beta);
+            } else if (d.beta.y == 0.0 && d.beta.x != 0.0) {  // real beta: two FMAs
+              const z64 cv = d.c[(size_t)row * d.ldc + j];
+              out = zmk(fma(d.beta.x, cv.x, out.x), fma(d.beta.x, cv.y, out.y));
             } else if (d.beta.x != 0.0 || d.beta.y != 0.0) {
               out = zadd(out, zmul(d.beta, d.c[(size_t)row * d.ldc + j]));
             }
