@@ -433,7 +433,9 @@ constexpr int RB_THREADS = 64;  // one thread per column; small CTAs spread the 
 // width nbo > 0 (two-level blocking) the solve stops at the end of the outer
 // block, K1 = min(K0 + nbo, s): columns from K1 on are swapped now and solved
 // later by the `far` variant, which applies no swaps and solves the rows of
-// this panel on columns K1..ncols-1 only.  One thread per column; NB >= nb is
+// this panel on columns K1..ncols-1 only.  The L factors left of the outer
+// block are never read again (only the right-hand sides are), so their rows
+// are left unswapped.  One thread per column; NB >= nb is
 // the compile-time panel width, and each dot product runs in two halves
 // (even / odd terms) to shorten the dependent FMA chains.
 template <int NB>
@@ -461,9 +463,12 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
     if (q >= d.ncols - K1) return;
     c = K1 + q;
   } else {
-    const int nout = d.ncols - nbw;
+    // columns left of the outer block (left of the panel with one level)
+    // hold L factors nothing reads again: they are not swapped
+    const int c0 = nbo > 0 ? (k0 / nbo) * nbo : k0;
+    const int nout = d.ncols - nbw - c0;
     if (q >= nout) return;
-    c = (q < k0) ? q : q + nbw;
+    c = (c0 + q < k0) ? c0 + q : c0 + q + nbw;
     for (int j = 0; j < nbw; ++j) {
       const int p = piv[j];
       if (p != k0 + j) {
