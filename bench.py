@@ -345,7 +345,8 @@ def main():
         inj_host = synth.make_injection(a.s_b, a.n_inj, seed=2, n_pts=P)
         inj_dev = torch.from_numpy(inj_host).cuda()
     stream.synchronize()
-    mine = pts[rank::world]   # this rank's points: a strided slice of the grid
+    from paper_1812_01396_gb300 import multi
+    mine = [pts[i] for i in multi.strided_shard(len(pts), rank, world)]  # equal-cost points: strided
 
     def batch(step):
         sel = [mine[(step * P + i) % len(mine)] for i in range(P)]

@@ -272,7 +272,7 @@ int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, con
 #define SS_KERNEL_TC_PACK_A  9  /* split-BF16 packing of A (3/6-product modes)        */
 #define SS_KERNEL_TC_PACK_B 10  /* split-BF16 packing of B                            */
 #define SS_KERNEL_TCGEMM    11  /* split-BF16 tcgen05 GEMM                            */
-#define SS_KERNEL_ZGEMM32   12  /* FP32-arithmetic complex GEMM                       */
+#define SS_KERNEL_ZGEMM32   12  /* (reserved: no FP32 GEMM is issued)                 */
 #define SS_KERNEL_OZ_SCALE  13  /* row/column power-of-two scales of the exact GEMM   */
 #define SS_KERNEL_OZ_PACK   14  /* BF16 digit slices of the exact GEMM                */
 #define SS_KERNEL_OZGEMM    15  /* digit-sliced tcgen05 GEMM, exact FP32 accumulation */

@@ -63,16 +63,8 @@ struct Cx<double> {
   static __device__ __forceinline__ T cvt(z64 v) { return v; }
   static __device__ __forceinline__ z64 back(T v) { return v; }
 };
-template <>
-struct Cx<float> {
-  typedef float2 T;
-  static __device__ __forceinline__ T cvt(z64 v) { return make_float2((float)v.x, (float)v.y); }
-  static __device__ __forceinline__ z64 back(T v) { return zmk((double)v.x, (double)v.y); }
-};
 
-// R = double: the FP64 kernel of the FP64 path.  R = float: operands are
-// rounded to FP32 on load and accumulated in FP32 (the low-rank LU updates of
-// the mixed path); C is still read and written in FP64.
+// R = double: complex128 operands and accumulation (the only instance).
 template <typename R, int V>
 __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ descs,
                                                    const int* __restrict__ tile_start, int nprob) {
@@ -205,12 +197,6 @@ void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total
     case 4: zgemm_kernel<double, 4><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob); break;
     default: zgemm_kernel<double, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
   }
-}
-
-void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
-                    cudaStream_t st) {
-  if (nprob <= 0 || total_tiles <= 0) return;
-  zgemm_kernel<float, 0><<<total_tiles, NT, 0, st>>>(d, tile_start, nprob);
 }
 
 }  // namespace ss

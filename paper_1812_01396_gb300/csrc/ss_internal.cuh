@@ -117,10 +117,6 @@ void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total
                   cudaStream_t st, int variant = 0);
 int zgemm_tiles(int m, int n, int variant = 0);  // CTAs one problem needs
 int zgemm_variant(const std::vector<GemmDesc>& ds);  // tile shape padding the group least
-// Same descriptors, FP32 arithmetic (operands rounded to FP32 on load, FP32
-// accumulation, FP64 C): the low-rank LU updates of the mixed path.
-void launch_zgemm32(const GemmDesc* d, const int* tile_start, int nprob, int total_tiles,
-                    cudaStream_t st);
 
 void launch_zform(const FormDesc* d, const int* tile_start, int nprob, int total_tiles,
                   cudaStream_t st);

@@ -273,12 +273,12 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
     if (upd == UPD_EXACT_TC || upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
-    else gemm(g, upd == UPD_FP32, upd == UPD_FP64);
+    else gemm(g, true);
   };
   // the nb-deep updates inside an outer block (two-level blocking)
   auto inner_update = [&](const std::vector<GemmDesc>& g) {
     if (upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
-    else gemm(g, false, true);
+    else gemm(g, true);
   };
   const int np = (int)ds.size();
   int smax = 0;
@@ -513,7 +513,6 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
         ++n;
         break;
       }
-      case K_GEMM32: launch_zgemm32((const GemmDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_LU_ROW:

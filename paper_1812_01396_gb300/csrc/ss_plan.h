@@ -81,16 +81,16 @@ class Plan {
 
   // fp32 = true: the FP32-arithmetic kernel (low-rank updates of the mixed path)
   // lu_label: account the launch as an LU update (profiling only)
-  void gemm(const std::vector<GemmDesc>& ds, bool fp32 = false, bool lu_label = false) {
+  void gemm(const std::vector<GemmDesc>& ds, bool lu_label = false) {
     if (ds.empty()) return;
-    const int variant = fp32 ? 0 : zgemm_variant(ds);
+    const int variant = zgemm_variant(ds);
     std::vector<int> start(ds.size());
     int tot = 0;
     for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zgemm_tiles(ds[i].m, ds[i].n, variant); }
     if (tot == 0) return;
     LaunchRec r;
     r.ival = variant;
-    r.kind = fp32 ? K_GEMM32 : (lu_label ? K_GEMM_LU : K_GEMM);
+    r.kind = lu_label ? K_GEMM_LU : K_GEMM;
     r.off = push_vec(ds);
     r.toff = push_vec(start);
     r.nprob = (int)ds.size();
@@ -128,7 +128,7 @@ class Plan {
   // Arithmetic of the rank-nb trailing and back-substitution updates
   // (panels, pivots and triangular blocks always stay FP64).
   // UPD_EXACT_ALL: the nb-deep updates inside an outer block too.
-  enum Updates { UPD_FP64 = 0, UPD_FP32 = 1, UPD_EXACT_TC = 2, UPD_EXACT_ALL = 3 };
+  enum Updates { UPD_FP64 = 0, UPD_EXACT_TC = 2, UPD_EXACT_ALL = 3 };
   // UPD_EXACT_TC slices the update operands into `pack` (cap bytes).
   // nbo > nb (a multiple of nb): two-level blocking; the depth-nbo
   // trailing and back-substitution updates use `upd`, the nb-deep updates
