@@ -161,6 +161,14 @@ long long ss_launch_count(const ss_handle* h);
 int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
              int transB, ss_c64* C, int ldc, void* stream);
 
+/* The exact GEMM's split for inner dimension k (host only, no GPU needed):
+ * slice width w (2k rounded up to 64), beta bits per digit, S digit slices,
+ * and the exact FP32 passes: pass p accumulates the digit pairs
+ * (t, pd[p] - t) for t = pt0[p] .. pt0[p] + pnp[p] - 1.  The arrays hold at
+ * least 32 entries.  Returns SS_ERR_ARG when k < 1 or no exact split exists. */
+int ss_exact_gemm_plan(int k, int* w, int* beta, int* S, int* npass, unsigned char* pd, unsigned char* pt0,
+                       unsigned char* pnp);
+
 /* Transmission from caller-provided blocks (the Caroli trace of the
  * transmission step): T[p] = Re Tr[Gamma_L G_1n Gamma_R G_1n^H] with
  * Gamma = i (Sigma - Sigma^H), for n_pts points of block size s_b.

@@ -31,7 +31,7 @@ EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_ener
            "ss_profile_reset", "ss_profile_read_issued", "ss_zgemm", "ss_caroli_transmission",
            "ss_caroli_transmission_noalloc", "ss_noalloc_last_error", "ss_mlp_create", "ss_mlp_destroy",
            "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward", "ss_mlp_train_step", "ss_mlp_last_error",
-           "ss_set_warm_start", "ss_surface_gf", "ss_autotune")
+           "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
                 "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
                 "oz_scale": 13, "oz_pack": 14, "ozgemm": 15, "frob2": 16, "zgemm_lu": 17, "ozgemm_lu": 18}
@@ -104,6 +104,9 @@ def load_library(path: str = LIB_PATH):
     lib.ss_set_warm_start.argtypes = [vp, vp, C.c_int, C.c_double]
     lib.ss_autotune.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, ip, ip, ip, dp]
     lib.ss_autotune.restype = C.c_int
+    ub = C.POINTER(C.c_ubyte)
+    lib.ss_exact_gemm_plan.argtypes = [C.c_int, ip, ip, ip, ip, ub, ub, ub]
+    lib.ss_exact_gemm_plan.restype = C.c_int
     lib.ss_surface_gf.argtypes = [vp, C.c_int, dp, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double, vp, ip, ip, ip]
     for name in ("ss_mlp_create", "ss_mlp_destroy", "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward",
                  "ss_mlp_train_step", "ss_set_warm_start", "ss_surface_gf"):
@@ -360,6 +363,18 @@ def ss_zgemm(A, B, C, precision=SS_FP64, transA=False, transB=False, stream=None
                       int(transB), _ptr(C), int(C.stride(0)), stream)
     if rc != SS_OK:
         raise SSError(rc, lib.ss_last_error(None).decode())
+
+
+def exact_gemm_plan(k):
+    """ss_exact_gemm_plan: (w, beta, S, passes) with passes a list of
+    (level, first t, number of pairs) for inner dimension k (no GPU needed)."""
+    lib = load_library()
+    w, beta, S, npass = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    pd, pt0, pnp = (C.c_ubyte * 64)(), (C.c_ubyte * 64)(), (C.c_ubyte * 64)()
+    rc = lib.ss_exact_gemm_plan(int(k), C.byref(w), C.byref(beta), C.byref(S), C.byref(npass), pd, pt0, pnp)
+    if rc != SS_OK:
+        raise SSError(rc, "no exact split for k = %d" % k)
+    return w.value, beta.value, S.value, [(pd[p], pt0[p], pnp[p]) for p in range(npass.value)]
 
 
 def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):

@@ -1654,6 +1654,24 @@ const char* ss_last_error(const ss_handle* h) {
 
 long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
 
+int ss_exact_gemm_plan(int k, int* w, int* beta, int* S, int* npass, unsigned char* pd, unsigned char* pt0,
+                       unsigned char* pnp) {
+  if (k < 1) return SS_ERR_ARG;
+  OzShape sh;
+  oz_plan(k, &sh);
+  if (sh.npass > OZ_MAXPASS) return SS_ERR_ARG;
+  if (w) *w = sh.w;
+  if (beta) *beta = sh.beta;
+  if (S) *S = sh.S;
+  if (npass) *npass = sh.npass;
+  for (int p = 0; p < sh.npass; ++p) {
+    if (pd) pd[p] = sh.pd[p];
+    if (pt0) pt0[p] = sh.pt0[p];
+    if (pnp) pnp[p] = sh.pnp[p];
+  }
+  return SS_OK;
+}
+
 int ss_zgemm(int precision, int m, int n, int k, const ss_c64* A, int lda, int transA, const ss_c64* B, int ldb,
              int transB, ss_c64* C, int ldc, void* stream) {
   if (m < 0 || n < 0 || k < 1 || !A || !B || !C || lda < 1 || ldb < 1 || ldc < n ||

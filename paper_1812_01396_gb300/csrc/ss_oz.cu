@@ -359,7 +359,8 @@ __device__ __forceinline__ long long fixed62(double x, int e) {
 }
 
 // Digit t of R is the round-to-nearest quotient by 2^{62 - beta (t+1)}, then
-// removed from R; |digit| <= 2^beta is an exact BF16 number.  Two values
+// removed from R (a digit past the 62 fixed-point bits, beta S > 62, is the
+// remainder scaled up, exactly); |digit| <= 2^beta is an exact BF16 number.  Two values
 // (adjacent columns) at a time, stored as one bfloat16 pair per slice.
 template <int S>
 __device__ __forceinline__ void write_digits2(__nv_bfloat16* row, int w, int off, int beta, double x0, double x1,
@@ -368,10 +369,18 @@ __device__ __forceinline__ void write_digits2(__nv_bfloat16* row, int w, int off
 #pragma unroll 3
   for (int t = 0; t < S; ++t) {
     const int sh = 62 - beta * (t + 1);
-    const long long h = 1ll << (sh - 1);
-    const long long q0 = (R0 + h) >> sh, q1 = (R1 + h) >> sh;
-    R0 -= q0 << sh;
-    R1 -= q1 << sh;
+    long long q0, q1;
+    if (sh > 0) {
+      const long long h = 1ll << (sh - 1);
+      q0 = (R0 + h) >> sh;
+      q1 = (R1 + h) >> sh;
+      R0 -= q0 << sh;
+      R1 -= q1 << sh;
+    } else {  // past the 62 fixed-point bits: the remainder itself, exactly
+      q0 = R0 << -sh;
+      q1 = R1 << -sh;
+      R0 = R1 = 0;
+    }
     *reinterpret_cast<__nv_bfloat162*>(row + (size_t)t * w + off) =
         __floats2bfloat162_rn((float)(int)q0, (float)(int)q1);
   }
@@ -383,8 +392,14 @@ __device__ __forceinline__ void write_digits1(__nv_bfloat16* row, int w, int off
 #pragma unroll 3
   for (int t = 0; t < S; ++t) {
     const int sh = 62 - beta * (t + 1);
-    const long long q = (R + (1ll << (sh - 1))) >> sh;
-    R -= q << sh;
+    long long q;
+    if (sh > 0) {
+      q = (R + (1ll << (sh - 1))) >> sh;
+      R -= q << sh;
+    } else {  // past the 62 fixed-point bits: the remainder itself, exactly
+      q = R << -sh;
+      R = 0;
+    }
     row[(size_t)t * w + off] = __float2bfloat16_rn((float)(int)q);
   }
 }
