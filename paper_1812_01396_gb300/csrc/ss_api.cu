@@ -9,7 +9,12 @@
 //      (Sec. 3B, "two accelerators" become two problem groups on one GPU);
 //   3. boundary correction of Eq. x: R = 1 - C Q, LU(R), z, x = Q (b' + z) and
 //      the corner G_1n of (A - B C)^-1;
-//   4. T = Re Tr[Gamma_L G_1n Gamma_R G_1n^H].
+//   4. T = Re Tr[Gamma_L G_1n Gamma_R G_1n^H];
+//   5. mixed path with x requested: refinement of x to a normwise backward
+//      error <= ir_tol (residual, block-UL correction with the kept D_i^-1,
+//      SMW correction with the kept R^-1).
+// In the mixed path every product is the exact digit-sliced tensor-core GEMM
+// (ss_oz.cu); pivoted panels and triangular blocks of the LU stay FP64.
 // Points are ordered longest-first by n_b * s_b^3 and cut into chunks that
 // fit the workspace allocated at ss_create (the batch scheduler).
 #include <cuda_runtime.h>

@@ -8,7 +8,8 @@
 // on ties (any stable order gives the same x).
 //
 // Per panel of nb <= 32 columns starting at k0 (right-looking):
-//   lu_panel    one CTA per problem factors rows k0..s-1 of the panel;
+//   lu_panel    rows k0..s-1 of the panel, on an 8-CTA cluster per problem
+//               (one CTA per problem for panels taller than 1024 rows);
 //   lu_rowblock applies the panel's row swaps to every other column and
 //               forms U12 = L11^-1 A12 (and L11^-1 B1) in place;
 //   (zgemm)     A22 -= L21 U12 over the trailing columns, RHS included.
