@@ -515,7 +515,7 @@ def main():
                        "n_inj": a.n_inj, "precision": "fp64" if head_prec == ss.SS_FP64 else "mixed (SS_MIXED_OZAKI)",
                        "parallelism": f"(E,k) shards x{world}",
                        "l2": "inputs larger than L2: per-step workspace "
-                             f"{P * (2 * a.n_b + 43) * a.s_b ** 2 * 16 / 1e9:.1f} GB"},
+                             f"{P * ((2 if head_prec == ss.SS_FP64 else 3) * a.n_b + 49) * a.s_b ** 2 * 16 / 1e9:.1f} GB"},
             "tflops": head["tflops"],
             "roofline": roofline,
             "kernels_ms": {k: round(v["ms"], 3) for k, v in kern.items()},
