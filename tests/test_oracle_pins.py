@@ -306,3 +306,25 @@ def test_backward_error_is_the_smallest_perturbation():
     # an exact solution has zero backward error
     M2 = np.diag([1.0, 2.0, 4.0])
     assert dense.backward_error(M2, np.array([[1.0], [0.5], [0.25]]), np.ones((3, 1))) == 0.0
+
+
+def test_oracle_reproduces_golden_small_case():
+    """The small case's stored oracle outputs (written by
+    tests/golden/make_golden.py from the oracle only) are reproduced: a guard
+    against unintended changes of the oracle's arithmetic."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_case.json")
+    gold = json.load(open(here))
+    dev = synth.make_device(16, 32, seed=1)[0]
+    inj = synth.make_injection(32, 4, seed=1)[0]
+    r = dense.solve_point(dev, 0.3, inj)
+    assert r["T"] == pytest.approx(gold["T"], rel=1e-11)
+    assert r["T_RL"] == pytest.approx(gold["T_RL"], rel=1e-11)
+    assert abs(r["T_imag"]) < 1e-12
+    assert np.linalg.norm(r["sigma_L"]) == pytest.approx(gold["norm_sigma_L"], rel=1e-11)
+    assert np.linalg.norm(r["sigma_R"]) == pytest.approx(gold["norm_sigma_R"], rel=1e-11)
+    assert np.linalg.norm(r["x"]) == pytest.approx(gold["norm_x"], rel=1e-11)
+    assert complex(*gold["sigma_L_00"]) == pytest.approx(complex(r["sigma_L"][0, 0]), rel=1e-10)
+    assert complex(*gold["x_00"]) == pytest.approx(complex(r["x"][0, 0]), rel=1e-10)
+    assert [r["info"]["iters_L"], r["info"]["iters_R"]] == gold["doubling_iters"]
