@@ -311,7 +311,9 @@ def test_backward_error_is_the_smallest_perturbation():
 def test_oracle_reproduces_golden_small_case():
     """The small case's stored oracle outputs (written by
     tests/golden/make_golden.py from the oracle only) are reproduced: a guard
-    against unintended changes of the oracle's arithmetic."""
+    against unintended changes of the oracle's arithmetic.  The tolerance
+    (1e-8) leaves room for another BLAS: the lead doubling at eta = 1e-10
+    amplifies rounding differences by up to about 1e6."""
     import json
     import os
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_case.json")
@@ -319,12 +321,12 @@ def test_oracle_reproduces_golden_small_case():
     dev = synth.make_device(16, 32, seed=1)[0]
     inj = synth.make_injection(32, 4, seed=1)[0]
     r = dense.solve_point(dev, 0.3, inj)
-    assert r["T"] == pytest.approx(gold["T"], rel=1e-11)
-    assert r["T_RL"] == pytest.approx(gold["T_RL"], rel=1e-11)
+    assert r["T"] == pytest.approx(gold["T"], rel=1e-8)
+    assert r["T_RL"] == pytest.approx(gold["T_RL"], rel=1e-8)
     assert abs(r["T_imag"]) < 1e-12
-    assert np.linalg.norm(r["sigma_L"]) == pytest.approx(gold["norm_sigma_L"], rel=1e-11)
-    assert np.linalg.norm(r["sigma_R"]) == pytest.approx(gold["norm_sigma_R"], rel=1e-11)
-    assert np.linalg.norm(r["x"]) == pytest.approx(gold["norm_x"], rel=1e-11)
-    assert complex(*gold["sigma_L_00"]) == pytest.approx(complex(r["sigma_L"][0, 0]), rel=1e-10)
-    assert complex(*gold["x_00"]) == pytest.approx(complex(r["x"][0, 0]), rel=1e-10)
+    assert np.linalg.norm(r["sigma_L"]) == pytest.approx(gold["norm_sigma_L"], rel=1e-8)
+    assert np.linalg.norm(r["sigma_R"]) == pytest.approx(gold["norm_sigma_R"], rel=1e-8)
+    assert np.linalg.norm(r["x"]) == pytest.approx(gold["norm_x"], rel=1e-8)
+    assert complex(*gold["sigma_L_00"]) == pytest.approx(complex(r["sigma_L"][0, 0]), rel=1e-7)
+    assert complex(*gold["x_00"]) == pytest.approx(complex(r["x"][0, 0]), rel=1e-7)
     assert [r["info"]["iters_L"], r["info"]["iters_R"]] == gold["doubling_iters"]
