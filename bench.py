@@ -429,8 +429,7 @@ def main():
 
     run_mixed = a.precision in ("mixed", "both")
     run_fp64 = a.precision in ("fp64", "both")
-    clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                              f"clocks_rank{rank}.csv"))
+    clk = Clocks(os.path.join(tempfile.gettempdir(), f"splitsolve_clocks_rank{rank}.csv"))
     head_prec = ss.SS_MIXED_OZAKI if run_mixed else ss.SS_FP64
     head = measure(head_prec, a.steps, a.warmup, clk)
     other = None

@@ -45,7 +45,7 @@ def test_bench_batch_against_oracle_samples(ss, tmp_path):
         assert np.all(np.asarray(st) == 0) and np.all(np.asarray(st2) == 0), (prec, st, st2)
         assert all(np.all(np.isfinite(np.asarray(x))) for x in xs)
         T[prec] = np.asarray(Tp)
-    # the target's bar for the mixed path: T within 1e-8 of FP64, and of the oracle
+    # the mixed path's bar: T within 1e-8 of the FP64 path, and both within 1e-8 of the oracle
     rel = np.abs(T[ss.SS_MIXED_OZAKI] - T[ss.SS_FP64]) / np.maximum(1.0, np.abs(T[ss.SS_FP64]))
     assert np.max(rel) <= 1e-8, rel
     for p in (0, 2):

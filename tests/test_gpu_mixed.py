@@ -3,7 +3,7 @@
 Its products run on the tcgen05 tensor cores from BF16 digit slices with
 exact FP32 accumulation, so it must meet the same bar as the FP64 path: 1e-10,
 or 20 times the oracle's one-ulp sensitivity (see test_gpu_parity).  The
-target's own bar for the mixed path (1e-8 on T) is checked as well.
+1e-8 bar on T for the mixed path is checked as well.
 """
 import numpy as np
 import pytest
