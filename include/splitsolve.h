@@ -190,11 +190,14 @@ int ss_caroli_transmission(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c
  * every GPU loading the library holds until the process exits; the call
  * allocates nothing.  Limits: n_pts <= 256 and n_pts*s_b*s_b <= 65536,
  * larger problems are rejected with SS_ERR_ARG.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  Every call reuses the same array:
+ * looks up the array's device address (cudaGetSymbolAddress).  The call
+ * synchronises `stream` and uploads its descriptors from host memory, so it
+ * cannot be captured into a CUDA graph: on a capturing stream it returns
+ * SS_ERR_ARG without enqueuing anything.  Every call reuses the same array:
  * calls that overlap on the GPU (other streams, other threads) race and must
  * be serialised by the caller.  No part of the array needs to start at zero.
- * Errors: SS_ERR_ARG, SS_ERR_CUDA; message in ss_noalloc_last_error(). */
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA; the message is in ss_noalloc_last_error(),
+ * which holds the text of the last failing call made by the CALLING thread. */
 int ss_caroli_transmission_noalloc(int n_pts, int s_b, const ss_c64* sigma_L, const ss_c64* sigma_R,
                                    const ss_c64* G1n, double* T, void* stream);
 const char* ss_noalloc_last_error(void);

@@ -377,9 +377,42 @@ def exact_gemm_plan(k):
     return w.value, beta.value, S.value, [(pd[p], pt0[p], pnp[p]) for p in range(npass.value)]
 
 
+def _check_caroli_args(sigma_L, sigma_R, G1n, T):
+    """Host-side checks of the Caroli entry points' tensors, so that nothing the
+    kernels would read or write out of bounds reaches the device: CUDA tensors
+    on the current device, complex128 blocks of one shape (P, s, s), a float64
+    T of at least P entries.  Returns (P, s)."""
+    import torch
+    named = (("sigma_L", sigma_L), ("sigma_R", sigma_R), ("G1n", G1n), ("T", T))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    cur = torch.cuda.current_device()
+    for name, t in named:
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    for name, t in named[:3]:
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{name} must be complex128, got {t.dtype}")
+    if T.dtype != torch.float64:
+        raise ValueError(f"T must be float64, got {T.dtype}")
+    if sigma_L.dim() != 3 or sigma_L.shape[1] != sigma_L.shape[2] or sigma_L.shape[1] < 1:
+        raise ValueError(f"sigma_L must have shape (P, s, s), got {tuple(sigma_L.shape)}")
+    for name, t in named[1:3]:
+        if tuple(t.shape) != tuple(sigma_L.shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, sigma_L has {tuple(sigma_L.shape)}")
+    P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
+    if T.numel() < P:
+        raise ValueError(f"T holds {T.numel()} entries, {P} are written")
+    return P, s
+
+
 def ss_caroli_transmission(sigma_L, sigma_R, G1n, T, stream=None):
     """T[p] = Re Tr[Gamma_L G Gamma_R G^H]; torch CUDA tensors (P,s,s) complex128 and (P,) float64."""
     lib = load_library()
+    _check_caroli_args(sigma_L, sigma_R, G1n, T)
     sigma_L, sigma_R, G1n, T = _dev_in(sigma_L), _dev_in(sigma_R), _dev_in(G1n), _dev_out(T)
     P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
     rc = lib.ss_caroli_transmission(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
@@ -394,10 +427,10 @@ def ss_caroli_transmission_noalloc(sigma_L, sigma_R, G1n, T, stream=None):
     :func:`ss_caroli_transmission`.  Limits: P <= 256, P*s^2 <= 65536.
     Inputs must already be contiguous: copying them would allocate."""
     lib = load_library()
+    P, s = _check_caroli_args(sigma_L, sigma_R, G1n, T)
     for t in (sigma_L, sigma_R, G1n, T):
         if not t.is_contiguous():
             raise ValueError("inputs and outputs must be contiguous (dense row-major)")
-    P, s = int(sigma_L.shape[0]), int(sigma_L.shape[1])
     rc = lib.ss_caroli_transmission_noalloc(P, s, _ptr(sigma_L), _ptr(sigma_R), _ptr(G1n), _ptr(T), stream)
     if rc != SS_OK:
         raise SSError(rc, lib.ss_noalloc_last_error().decode())

@@ -40,7 +40,9 @@ static __device__ __align__(256) unsigned char g_na_scratch[NA_TOTAL_BYTES];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 void* g_na_addr[NA_MAX_DEVICES] = {nullptr};
-std::string g_na_error;
+// The error text belongs to the calling thread, so callers on different
+// threads (e.g. one per device) never overwrite each other's message.
+thread_local std::string g_na_error;
 
 // Device address of the scratch on the current device, looked up once per
 // device (the first call on a device does this set-up).
@@ -88,10 +90,16 @@ extern "C" int ss_caroli_transmission_noalloc(int n_pts, int s_b, const ss_c64* 
   if (n_pts > NA_MAX_POINTS || (size_t)n_pts * s_b * s_b > NA_MAX_ELEMS)
     return na_fail(SS_ERR_ARG, "problem exceeds the static scratch: need n_pts <= 256 and n_pts*s_b^2 <= 65536, got n_pts=" +
                                    std::to_string(n_pts) + " s_b=" + std::to_string(s_b));
-  void* base = nullptr;
-  cudaError_t e = scratch_address(&base);
-  if (e != cudaSuccess) return na_fail(SS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t st = (cudaStream_t)stream;
+  // The call synchronises its stream and copies its descriptors from a
+  // temporary host buffer, so it cannot be recorded into a CUDA graph.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return na_fail(SS_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone) return na_fail(SS_ERR_ARG, "the stream is being captured; this call cannot be captured");
+  void* base = nullptr;
+  e = scratch_address(&base);
+  if (e != cudaSuccess) return na_fail(SS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   unsigned char* dbase = static_cast<unsigned char*>(base);
   z64* data = reinterpret_cast<z64*>(dbase);
   unsigned char* desc = dbase + NA_DATA_BYTES;

@@ -49,21 +49,30 @@ def gather_values(values, indices, n_points: int) -> np.ndarray:
     import torch
     import torch.distributed as dist
 
+    dev = _comm_device()
     local = torch.tensor(np.stack([np.asarray(indices, np.float64), np.asarray(values, np.float64)], 1)
-                         if len(indices) else np.zeros((0, 2)), dtype=torch.float64)
+                         if len(indices) else np.zeros((0, 2)), dtype=torch.float64, device=dev)
     world = dist.get_world_size()
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(sizes, torch.tensor([local.shape[0]], dtype=torch.int64))
+    sizes = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(sizes, torch.tensor([local.shape[0]], dtype=torch.int64, device=dev))
     cap = int(max(int(s) for s in sizes))
-    pad = torch.full((cap, 2), float("nan"), dtype=torch.float64)
+    pad = torch.full((cap, 2), float("nan"), dtype=torch.float64, device=dev)
     pad[:local.shape[0]] = local
-    bufs = [torch.empty((cap, 2), dtype=torch.float64) for _ in range(world)]
+    bufs = [torch.empty((cap, 2), dtype=torch.float64, device=dev) for _ in range(world)]
     dist.all_gather(bufs, pad)
     out = np.full(n_points, np.nan)
     for b, n in zip(bufs, sizes):
-        b = b[:int(n)].numpy()
+        b = b[:int(n)].cpu().numpy()
         out[b[:, 0].astype(np.int64)] = b[:, 1]
     return out
+
+
+def _comm_device():
+    """Tensors of a host-side exchange live on the GPU under NCCL, on the host under gloo."""
+    import torch
+    import torch.distributed as dist
+
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
 
 
 def max_over_ranks(v: float) -> float:
@@ -71,6 +80,6 @@ def max_over_ranks(v: float) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([float(v)], dtype=torch.float64)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=_comm_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())

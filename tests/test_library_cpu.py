@@ -77,3 +77,14 @@ def test_create_reports_missing_device(lib):
     assert rc == ss.SS_ERR_CUDA
     assert h.value is None
     assert b"device" in lib.ss_last_error(None).lower()
+
+
+def test_caroli_entry_points_reject_host_tensors_before_any_launch(lib):
+    """CPU tensors (or anything not a CUDA tensor) are refused by the binding
+    with ValueError, so no kernel can be handed a host pointer."""
+    import torch
+    a = torch.zeros((2, 4, 4), dtype=torch.complex128)
+    T = torch.zeros(2, dtype=torch.float64)
+    for fn in (ss.ss_caroli_transmission, ss.ss_caroli_transmission_noalloc):
+        with pytest.raises(ValueError):
+            fn(a, a, a, T)

@@ -1,7 +1,8 @@
 """Multi-process host logic of the N-GPU path, on CPU ranks (gloo, world 2):
 the LPT partition covers every point once and is balanced, the gather
-rebuilds the serial result, and the step time is the maximum over ranks."""
-import math
+rebuilds the serial result (the oracle's T of every point of an uneven batch,
+each computed on the rank LPT gave it), and the step time is the maximum over
+ranks."""
 import os
 import socket
 
@@ -25,8 +26,18 @@ def _points():
     return pts, [multi.point_cost(n, s) for (s, n, _, _) in pts]
 
 
-def _fake_T(E, k):
-    return math.sin(3.0 * E) + 0.25 * math.cos(k)
+def _small_points():
+    """Uneven small points (s_b, n_b, E, k) whose oracle T a CPU rank computes in
+    milliseconds: the same kind of work a GPU rank shards, at a tenth of the size."""
+    pts = synth.uneven_points(14, seed=5, s_choices=(4, 6, 8), n_choices=(2, 3, 5))
+    return pts, [multi.point_cost(n, s) for (s, n, _, _) in pts]
+
+
+def _oracle_T(pt):
+    from oracle import dense
+    s, n, E, k = pt
+    dev = synth.make_device(n, s, seed=100 + 7 * s + n, k_points=(k,), w_scale=0.25)[0]
+    return float(dense.solve_point(dev, E)["T"])
 
 
 def _rank_main(rank, world, port, out):
@@ -35,9 +46,9 @@ def _rank_main(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        pts, costs = _points()
+        pts, costs = _small_points()
         mine = multi.lpt_shard(costs, world)[rank]
-        T = [_fake_T(pts[i][2], pts[i][3]) for i in mine]
+        T = [_oracle_T(pts[i]) for i in mine]
         full = multi.gather_values(T, mine, len(pts))
         slowest = multi.max_over_ranks(1.0 + rank)
         if rank == 0:
@@ -69,7 +80,7 @@ def test_gather_and_max_over_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    pts, _ = _points()
-    ref = [_fake_T(E, k) for (_, _, E, k) in pts]
-    assert np.allclose(full, ref, rtol=0, atol=0)
+    pts, _ = _small_points()
+    ref = [_oracle_T(pt) for pt in pts]
+    assert np.array_equal(np.asarray(full), np.asarray(ref))  # same arithmetic on every rank: bit-equal
     assert slowest == 2.0

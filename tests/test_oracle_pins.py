@@ -330,3 +330,105 @@ def test_oracle_reproduces_golden_small_case():
     assert complex(*gold["sigma_L_00"]) == pytest.approx(complex(r["sigma_L"][0, 0]), rel=1e-7)
     assert complex(*gold["x_00"]) == pytest.approx(complex(r["x"][0, 0]), rel=1e-7)
     assert [r["info"]["iters_L"], r["info"]["iters_R"]] == gold["doubling_iters"]
+
+
+# ------------------------------------------------------------ MLP forward
+def test_mlp_forward_hand_computed_network():
+    """A 3 -> 2 -> 2 -> 3 network whose pre-activations are +-ln 3 and 0, where
+    SiLU is known in closed form: sigma(ln 3) = 3/4, so SiLU(ln 3) = 0.75 ln 3,
+    SiLU(-ln 3) = -0.25 ln 3, SiLU(0) = 0.  The square middle layer is not
+    symmetric, so W in place of W^T changes the result; the first and last
+    layers are not square, so a transposed layout fails outright."""
+    L = math.log(3.0)
+    W1 = np.array([[L, 0.0, 0.0], [0.0, 0.0, L]])
+    b1 = np.zeros(2)
+    W2 = np.array([[1.0, -1.0], [1.0, 3.0]])
+    b2 = np.zeros(2)
+    W3 = np.array([[2.0, 5.0], [0.0, 1.0], [-4.0, 7.0]])
+    b3 = np.array([0.5, 0.0, 1.0])
+    x = np.array([[1.0, 2.0, -1.0]])
+    y, cache = mlp.forward([W1, b1, W2, b2, W3, b3], x)
+    _, h1, a1, h2, a2 = cache
+    assert np.allclose(h1, [[L, -L]], rtol=0, atol=1e-15)
+    assert np.allclose(a1, [[0.75 * L, -0.25 * L]], rtol=0, atol=1e-15)
+    assert np.allclose(h2, [[L, 0.0]], rtol=0, atol=1e-15)
+    assert np.allclose(a2, [[0.75 * L, 0.0]], rtol=0, atol=1e-15)
+    assert np.allclose(y, [[1.5 * L + 0.5, 0.0, -3.0 * L + 1.0]], rtol=0, atol=1e-14)
+
+
+def test_mlp_silu_identities():
+    """SiLU(0) = 0, SiLU(-x) = SiLU(x) - x, SiLU(x) -> x for large x."""
+    xs = np.array([0.3, 1.7, 4.0, 12.0])
+    assert mlp.silu(np.array([0.0]))[0] == 0.0
+    assert np.allclose(mlp.silu(-xs), mlp.silu(xs) - xs, rtol=0, atol=1e-15)
+    assert abs(mlp.silu(np.array([40.0]))[0] - 40.0) < 1e-15
+
+
+def test_mlp_features_at_known_angles():
+    """Feature order (E, cos k, sin k, sin(m pi E), cos(m pi E), m = 1..8) at
+    E = 1/2, k = pi/2, where every entry is 0 or +-1."""
+    f = mlp.features([0.5], [math.pi / 2])[0]
+    assert f.shape == (19,)
+    assert f[0] == 0.5
+    assert abs(f[1]) < 1e-15 and abs(f[2] - 1.0) < 1e-15
+    sin_m = [1, 0, -1, 0, 1, 0, -1, 0]
+    cos_m = [0, -1, 0, 1, 0, -1, 0, 1]
+    for m in range(8):
+        assert abs(f[3 + 2 * m] - sin_m[m]) < 1e-14
+        assert abs(f[4 + 2 * m] - cos_m[m]) < 1e-14
+
+
+# ------------------------------------------------------ seeded fixed point
+@pytest.mark.parametrize("E", [-2.5, 3.0])
+def test_fixed_point_converges_to_chain_closed_form_out_of_band(E):
+    """s = 1 chain, out of band: the map g <- (D - U g L)^-1 contracts by
+    |lambda|^2 < 1 and its fixed point is g_R = Sigma / t^2 with Sigma = t lambda,
+    lambda the decaying root (the closed form of the decimation pins)."""
+    eps0, t = 0.2, -0.7
+    z = E + 1j * leads.DEFAULT_ETA
+    D = np.array([[z - eps0]])
+    U = np.array([[-t + 0j]])
+    L = np.array([[-t + 0j]])
+    # Sigma^2 - (z - eps0) Sigma + t^2 = 0 at the complex z of the map
+    dz = z - eps0
+    sq = np.sqrt(complex(dz * dz - 4 * t * t))
+    roots = np.array([(dz + sq) / 2, (dz - sq) / 2])
+    sigma = roots[np.argmin(np.abs(roots))]
+    assert abs(sigma / t) < 1
+    for side in ("R", "L"):
+        g = warm.fixed_point(np.zeros((1, 1)), D, U, L, side=side, iters=60)
+        assert abs(g[0, 0] - sigma / t ** 2) < 1e-13
+        assert warm.dyson_residual(g, D, U, L, side) < 1e-14
+
+
+@pytest.mark.parametrize("E", [-0.4, 0.7])
+def test_fixed_point_keeps_the_doubling_result(E):
+    """For a random lead (U != L^T, so the order U g L versus L g U matters) the
+    surface Green's function of the independent doubling is a fixed point of the
+    map of each side: one step moves it only by rounding."""
+    cell = _random_lead(6, 31)
+    z = E + 1j * leads.DEFAULT_ETA
+    D, U, Lm = leads.lead_matrices(cell, z)
+    for side in ("R", "L"):
+        g, _, conv = leads.surface_gf(cell, z, side)
+        assert conv
+        g1 = warm.fixed_point(g, D, U, Lm, side=side, iters=1)
+        assert np.linalg.norm(g1 - g) / np.linalg.norm(g) < 1e-9
+        other = "L" if side == "R" else "R"
+        g_wrong = warm.fixed_point(g, D, U, Lm, side=other, iters=1)
+        assert np.linalg.norm(g_wrong - g) / np.linalg.norm(g) > 1e-3
+
+
+# ----------------------------------------------------------- open channels
+def test_open_channels_of_decoupled_wire_closed_form():
+    """Decoupled wire: chain j carries one right-moving mode iff |E - eps_j| < 2|t|."""
+    s, t = 10, -0.8
+    dev, eps = synth.decoupled_wire(s, 3, t, seed=4)
+    cell = (dev.H_diag[0], dev.H_up[0], dev.S_diag[0], dev.S_up[0])
+    for E in (-2.1, -0.9, 0.05, 1.3, 2.4):
+        edges = np.concatenate([eps - 2 * abs(t), eps + 2 * abs(t)])
+        if np.min(np.abs(E - edges)) < 0.02:
+            continue
+        expect = int(np.sum(np.abs(E - eps) < 2 * abs(t)))
+        m, n_unit = channels.open_channels(cell, E)
+        assert m == expect and n_unit == 2 * expect
