@@ -52,6 +52,10 @@ def parse():
                          "dense random blocks (default n_b 48, s_b 2048), mixed vs FP64 vs oracle on few "
                          "points.  uneven and dense print their own JSON line")
     ap.add_argument("--points", type=int, default=2, help="dense workload: points of the mixed path")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the c1 latency, c3 uneven-batch and c4 dense-block sub-measurements")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps of the per-kernel event-timed pass (kernel shares and the roofline)")
     ap.add_argument("--gemm", default=None, metavar="MxNxK",
                     help="time one complex GEMM through ss_zgemm (exact tensor-core and FP64 kernels) "
                          "instead of the pipeline; prints its own JSON line")
@@ -152,6 +156,20 @@ def cpu_baseline(devs, pts, inj, budget_s=30.0):
     return {"value": done / dt, "unit": "(E,k) solves/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{done} (E,k) point(s) of the workload (the first timed ones), FP64 numpy RGF + "
                       f"Sancho-Rubio doubling, {dt:.1f} s"}, Ts
+
+
+def oracle_sensitivity(dev, E, inj, T_ref):
+    """Change of the oracle's T under two relative 2^-52 perturbations of H: the
+    conditioning floor any FP64 implementation of this point sees."""
+    rng = np.random.default_rng(1234)
+    out = 0.0
+    for _ in range(2):
+        d2 = synth.Device(dev.H_diag * (1 + 2.0 ** -52 * rng.standard_normal(dev.H_diag.shape)),
+                          dev.H_up * (1 + 2.0 ** -52 * rng.standard_normal(dev.H_up.shape)),
+                          dev.S_diag, dev.S_up)
+        T2 = float(oracle_point(d2, E, inj)["T"])
+        out = max(out, abs(T2 - T_ref) / max(1.0, abs(T_ref)))
+    return out
 
 
 def run_reference(a):
@@ -303,6 +321,126 @@ def run_dense(a):
     print(json.dumps(out), flush=True)
 
 
+def committed_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, valid
+    only while the kernel's source is the one the counters were taken on (the
+    summary records the SHA-256 of that source); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_nanowire_nb64_sb512.txt")
+    if not os.path.exists(path):
+        return None, "no committed capture"
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    src = os.path.join(ROOT, fields.get("source", ""))
+    if not os.path.exists(src) or "source_sha256" not in fields or "dram_bytes_per_launch" not in fields:
+        return None, "capture incomplete"
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != fields["source_sha256"]:
+        return None, f"kernel source changed since {os.path.basename(path)} was captured"
+    return float(fields["dram_bytes_per_launch"]), f"profiles/{os.path.basename(path)}"
+
+
+def run_c1(ss, torch):
+    """Single-point latency on the smallest workload: n_b = 16, s_b = 32,
+    E = 0.3, k = 0 (seed 1), 4 injected columns; the whole pipeline (self-energies,
+    sweeps, boundary, x, T) per call, host buffers, one point per call."""
+    dev = synth.make_device(16, 32, seed=1)[0]
+    inj = synth.make_injection(32, 4, seed=1)[0]
+    out = {"workload": "n_b=16, s_b=32, one (E,k) point (E=0.3, k=0), n_inj=4, host buffers", "unit": "us per solve"}
+    for name, prec in (("fp64", ss.SS_FP64), ("mixed", ss.SS_MIXED_OZAKI)):
+        h = ss.Handle(n_b_max=16, s_b_max=32, max_points=1, max_inj=4, precision=prec)
+        h.set_device(0, dev)
+        for _ in range(3):
+            h.solve([0.3], [0], [inj])
+            h.transmission([0.3], [0])
+        reps = 20
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            h.solve([0.3], [0], [inj])      # self-energies, sweeps, boundary, x (and T on the way)
+            T, _, st, _ = h.transmission([0.3], [0])  # cached T of the same point
+        dt = (time.perf_counter() - t0) / reps
+        l0 = h.launch_count()
+        h.solve([0.3], [0], [inj])
+        out[name] = {"us_per_solve": dt * 1e6, "launches_per_solve": h.launch_count() - l0, "T": float(T[0]),
+                     "status": int(st[0])}
+        h.close()
+    return out
+
+
+def run_c3(ss, torch, rank, world):
+    """Uneven batch, reduced sample of the 256-point workload: 8 devices of
+    (s_b, n_b) drawn from {256,384,512} x {32,64,128} (seed 3), 4 energies each
+    (32 points), mixed path: one batched call (grouped launches, CUDA graphs,
+    autotuned LU, chunks of 8 points) against one call per point on the same
+    handle.  With several ranks the points are split by LPT over the per-point
+    cost model and the transmissions are gathered on the host."""
+    from paper_1812_01396_gb300 import multi
+    shapes = synth.uneven_points(8, seed=3)
+    rng = np.random.default_rng(3)
+    pts = []
+    for d, (s_b, n_b, _, _) in enumerate(shapes):
+        for _ in range(4):
+            pts.append((d, float(rng.uniform(-1.0, 1.0))))
+    costs = [multi.point_cost(shapes[d][1], shapes[d][0]) for d, _ in pts]
+    mine = multi.lpt_shard(costs, world)[rank] if world > 1 else list(range(len(pts)))
+    used = sorted({pts[i][0] for i in mine})
+    h = ss.Handle(n_b_max=128, s_b_max=512, max_points=8, max_inj=1, precision=ss.SS_MIXED_OZAKI)
+    for d in used:
+        s_b, n_b = shapes[d][0], shapes[d][1]
+        dev = synth.make_device(n_b, s_b, seed=30 + d, band=s_b // 20, s_pert=0.02,
+                                k_points=(synth.K_POINTS_4[d % 4],), w_scale=0.25)[0]
+        h.set_device(d, dev)
+        del dev
+    for s_b in sorted({shapes[d][0] for d in used}):
+        h.autotune(s_b, 16, os.path.join(tempfile.gettempdir(), "splitsolve_autotune.txt"))
+    E = [pts[i][1] for i in mine]
+    K = [pts[i][0] for i in mine]
+    h.transmission(E[:8], K[:8])  # warm-up
+    (Tb, _, stb, _), tb = _timed(lambda: h.transmission(E, K))
+    Tp, sp = np.zeros(len(E)), np.zeros(len(E), np.int32)
+
+    def per_point():
+        for i in range(len(E)):
+            T, _, st, _ = h.transmission([E[i]], [K[i]])
+            Tp[i], sp[i] = T[0], st[0]
+    _, tp = _timed(per_point)
+    h.close()
+    T_all = multi.gather_values(np.asarray(Tb), mine, len(pts)) if world > 1 else np.asarray(Tb)
+    tb_max = multi.max_over_ranks(tb) if world > 1 else tb
+    tp_max = multi.max_over_ranks(tp) if world > 1 else tp
+    diff = float(np.max(np.abs(np.asarray(Tb) - Tp) / np.maximum(1.0, np.abs(Tp))))
+    return {"workload": "uneven: 32 (E,k) points over 8 devices " + str([sh[:2] for sh in shapes]) +
+                        " (s_b, n_b), mixed path", "unit": "(E,k) solves/s", "ranks": world,
+            "batched": len(pts) / tb_max, "per_point_calls": len(pts) / tp_max, "speedup": tp_max / tb_max,
+            "max_rel_T_diff_batched_vs_per_point": diff, "T_gathered": bool(np.all(np.isfinite(T_all))),
+            "status_ok": bool(np.all(np.asarray(stb) == 0) and np.all(sp == 0))}
+
+
+def run_c4(ss, torch):
+    """Dense random blocks n_b = 48, s_b = 2048 (seed 4), energies of the 32-point
+    grid on [-1, 1] at k = 0: the mixed path on 2 points, the FP64 path on the
+    first one, T compared; the refined x's backward error per point."""
+    n_b, s_b = 48, 2048
+    dev = synth.make_device(n_b, s_b, seed=4, s_pert=0.05)[0]
+    Es = [float(e) for e in synth.energy_grid(32)][:2]
+    out = {"workload": f"dense random blocks, n_b={n_b}, s_b={s_b}, k=0, E = first 2 of a 32-point grid on [-1,1]",
+           "unit": "s per (E,k) point"}
+    Ts = {}
+    for name, prec, pts in (("mixed", ss.SS_MIXED_OZAKI, Es), ("fp64", ss.SS_FP64, Es[:1])):
+        h = ss.Handle(n_b_max=n_b, s_b_max=s_b, max_points=len(pts), max_inj=1, precision=prec)
+        h.set_device(0, dev)
+        (T, err, st, _), t = _timed(lambda: h.transmission(pts, [0] * len(pts)))
+        h.close()
+        Ts[name] = np.asarray(T)
+        out[name] = {"points": len(pts), "s_per_point": t / len(pts), "status": [int(v) for v in st],
+                     "T": [float(v) for v in T]}
+    out["rel_T_mixed_vs_fp64"] = float(abs(Ts["mixed"][0] - Ts["fp64"][0]) / max(1.0, abs(Ts["fp64"][0])))
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -415,7 +553,7 @@ def main():
         with torch.cuda.stream(stream):
             step(hp, 0, inj_dev)
             hp.profile_reset()
-            for s_ in range(start, start + steps):
+            for s_ in range(start, start + min(steps, max(a.profile_steps, 1))):
                 step(hp, s_, inj_dev)
         stream.synchronize()
         kern = {}
@@ -434,7 +572,7 @@ def main():
     head = measure(head_prec, a.steps, a.warmup, clk)
     other = None
     if run_mixed and run_fp64:
-        # the plain FP64 path on the same points (fewer steps: ~9 s per step)
+        # the plain FP64 path on the same points (fewer steps: ~8 s per step)
         other = measure(ss.SS_FP64, min(a.steps, 2), 1, start=a.warmup)
 
     # live roofline of the dominant kernel: the exact tensor-core GEMM (mixed)
@@ -454,15 +592,27 @@ def main():
     else:
         g = {k2: kern["ozgemm"][k2] + kern["ozgemm_lu"][k2] for k2 in ("ms", "launches", "flops", "issued")}
         ms = g["ms"]
-        # tensor-pipe flops actually issued (digit pairs x padded slice width)
+        # achieved = the method's own work: 8 real flops per complex multiply-add
+        # (8 m n k per complex product), whatever the digit split issues
         alg = g["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        # what the tensor pipe executes: digit pairs x padded slice width
         tensor = g["issued"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-        pk = peaks.get("bf16_tflops_sustained") or 1700.0
-        roofline = {"bound": "tensor", "achieved": tensor, "peak": pk, "unit": "TFLOP/s", "frac": tensor / pk,
-                    "traffic": None, "kernel": "oz_gemm_kernel (digit-sliced BF16 tcgen05, exact FP32 accumulation)",
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
-                    "algorithmic_complex_fp64_equiv_tflops": alg,
-                    "avg_launch_ms": ms / max(g["launches"], 1), "share_of_kernel_time": ms / tot_ms}
+        pk = peaks.get("bf16_tflops_sustained")
+        src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; kernel timed inside a long step)"
+        if not pk:
+            pk, src = 1700.0, "fallback sustained bf16 figure (MEASURED_PEAKS.json absent)"
+        traffic, traffic_src = committed_traffic("oz_gemm")
+        launches = max(g["launches"], 1)
+        roofline = {"bound": "tensor", "achieved": alg, "peak": pk, "unit": "TFLOP/s", "frac": alg / pk,
+                    "traffic": traffic, "traffic_source": traffic_src,
+                    "kernel": "oz_gemm_kernel (digit-sliced BF16 tcgen05, exact FP32 accumulation)",
+                    "basis": "algorithmic complex-equivalent flops (8 per complex multiply-add, 8 m n k per product) "
+                             "of every exact-GEMM launch of the profiled steps / their CUDA-event time",
+                    "peak_source": src,
+                    "algorithmic_flops_per_launch": g["flops"] / launches,
+                    "tensor_pipe_issued_tflops": tensor, "tensor_pipe_issued_frac": tensor / pk,
+                    "issued_over_algorithmic": g["issued"] / max(g["flops"], 1.0),
+                    "avg_launch_ms": ms / launches, "share_of_kernel_time": ms / tot_ms}
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -474,16 +624,24 @@ def main():
             step(he, 0, inj_list)
         stream.synchronize()
         barrier()
+        e2e_steps = min(a.steps, 5)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for s_ in range(a.warmup, a.warmup + a.steps):
+            for s_ in range(a.warmup, a.warmup + e2e_steps):
                 step(he, s_, inj_list)
         stream.synchronize()
         te = max_over_ranks(time.perf_counter() - t0)
         he.close()
-        e2e = {"value": P * a.steps * world / te, "unit": "(E,k) solves/s",
+        e2e = {"value": P * e2e_steps * world / te, "unit": "(E,k) solves/s", "steps": e2e_steps,
                "h2d_bytes_per_step": P * 2 * a.s_b * a.n_inj * 16,
                "d2h_bytes_per_step": P * a.n_b * a.s_b * a.n_inj * 16 + P * 8}
+
+    extras = {}
+    if not a.no_extras:
+        extras["c1"] = run_c1(ss, torch) if rank == 0 else None
+        extras["c3"] = run_c3(ss, torch, rank, world)
+        extras["c4"] = run_c4(ss, torch) if rank == 0 else None
+        barrier()
 
     if rank == 0:
         cpu, vs_oracle = None, None
@@ -492,10 +650,24 @@ def main():
             cpu, T_or = cpu_baseline(devs, first, inj_host[0])
             n_or = len(T_or)
             rel = lambda T: max(abs(x - y) / max(1.0, abs(y)) for x, y in zip(T[:n_or], T_or))
-            vs_oracle = {"points": n_or, "max_rel_T_err_" + ("fp64" if head_prec == ss.SS_FP64 else "mixed"):
-                         rel(head["T"])}
+            hk = "fp64" if head_prec == ss.SS_FP64 else "mixed"
+            vs_oracle = {"points": n_or, "max_rel_T_err_" + hk: rel(head["T"])}
             if other is not None:
                 vs_oracle["max_rel_T_err_fp64"] = rel(other["T"])
+            # per point: errors of both paths next to the oracle's own one-ulp
+            # sensitivity (first sampled point; two extra oracle solves)
+            per = []
+            for i in range(n_or):
+                E_i, k_i = first[i]
+                d = {"E": E_i, "k_id": k_i, "T_oracle": T_or[i],
+                     "rel_err_" + hk: abs(head["T"][i] - T_or[i]) / max(1.0, abs(T_or[i]))}
+                if other is not None:
+                    d["rel_err_fp64"] = abs(other["T"][i] - T_or[i]) / max(1.0, abs(T_or[i]))
+                if i == 0:
+                    d["oracle_one_ulp_sensitivity"] = oracle_sensitivity(devs[k_i], E_i, inj_host[0], T_or[i])
+                    d["parity_bar"] = max(1e-10, 20.0 * d["oracle_one_ulp_sensitivity"])
+                per.append(d)
+            vs_oracle["per_point"] = per
         cmp = None
         if other is not None:
             nT = len(other["T"])
@@ -528,6 +700,9 @@ def main():
             "lu_tune": {("fp64" if k == ss.SS_FP64 else "mixed"): {"panel_width": v[0], "outer_width": v[1],
                                                                   "update": v[2], "ms": v[3]}
                         for k, v in tune.items()},
+            "c1": extras.get("c1"),
+            "c3": extras.get("c3"),
+            "c4": extras.get("c4"),
             "status_ok": head["ok"],
             "status_counts": {str(int(k)): int(v) for k, v in zip(*np.unique(head["status"], return_counts=True))},
             "err_est_max": float(np.max(head["err"])),

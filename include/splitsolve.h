@@ -74,16 +74,34 @@ typedef struct {
   int decim_max_iter; /* doubling cap -> SS_ERR_NOT_CONVERGED (default 100)           */
   double ir_tol;      /* mixed: refinement target: backward error <= ir_tol (1e-14)   */
   int ir_max_iter;    /* mixed: refinement cap (default 10)                            */
-  int warm_start;     /* reserved: 1 seeds the surface GF from a trained network       */
+  int warm_start;     /* 1: in ss_self_energy / ss_solve / ss_transmission / ss_dos,
+                         seed the surface GF of each lead that has a network attached
+                         (ss_set_warm_start) for points of the network's block size:
+                         network seed, at most 8 steps of g <- (D - U g L)^-1, accepted
+                         when the FP64 Dyson residual ||g (D - U g L) - 1||_F / sqrt(s_b)
+                         is <= 1e-10, otherwise the plain doubling.  Default 0.       */
   void* stream;       /* cudaStream_t to enqueue on (NULL = legacy default stream)     */
   int device_ptrs;    /* 1: array arguments are device pointers                        */
   int use_graphs;     /* 1: replay decimation iterations from captured CUDA graphs     */
   int profile;        /* 1: time every kernel launch with CUDA events (eager launches,
                          no graphs); read the totals with ss_profile_read            */
+  int partitions;     /* split every device into this many contiguous partitions whose
+                         block sweeps run concurrently (Sec. 3B, Fig. pp), merged by one
+                         Sherman-Morrison-Woodbury system of 2*partitions*s_b rows;
+                         1..8, default 1 (SplitSolve's plain two-column split)        */
+  int memory_lean;    /* 1: size the workspace for transmission-only calls
+                         (ss_transmission, ss_solve with x = NULL), which keep only the
+                         corner blocks of the inverse (running products) instead of both
+                         block columns: (31 + 16 P + 4 P^2) s_b^2 complex per point
+                         for P partitions (51 s_b^2 for one) instead of about
+                         (2 n_b + 45) s_b^2 in FP64 with one partition.  Calls that
+                         return wave functions or the density of states then fit fewer
+                         points per batch, or fail with SS_ERR_OOM.  Default 0.        */
 } ss_config;
 
 /* Fill *cfg with the defaults listed above (n_b_max = 64, s_b_max = 512,
- * max_points = 8, max_inj = 64, SS_FP64, host pointers, graphs on, profiling off). */
+ * max_points = 8, max_inj = 64, SS_FP64, host pointers, graphs on, profiling off,
+ * one partition, full workspace). */
 void ss_config_default(ss_config* cfg);
 
 /* Create a handle bound to the current CUDA device; allocates the device
@@ -109,7 +127,8 @@ int ss_set_hamiltonian(ss_handle* h, int k_id, int n_b, int s_b,
  * Sigma_L = A_{1,0} g_L A_{0,1}, Sigma_R = A_{n,n+1} g_R A_{n+1,n} (A at real E,
  * surface Green's functions g at E + i*eta by doubling).  sigma_L/sigma_R
  * (optional, may be NULL): s_b*s_b per point.  iters (optional, host):
- * 2 per point (left, right doubling steps).  status (optional, host): per
+ * 2 per point (left, right doubling steps; -8 for a lead whose warm start was
+ * accepted, cfg.warm_start).  status (optional, host): per
  * point SS_OK / SS_ERR_NOT_CONVERGED / SS_ERR_SINGULAR.  The results are
  * kept in the handle for later ss_solve / ss_transmission on the same
  * (E, k_id).  Returns the first non-OK point status, or a call-level error. */
@@ -120,7 +139,8 @@ int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id,
  * first and last block rows (Eq. wf; Steps 1-4 of Eq. x).  inj: per point
  * 2*s_b x n_inj row-major (rows of block 1, then rows of block n_b).
  * x: per point (n_b*s_b) x n_inj row-major; may be NULL, in which case only
- * the factors and G_1n are computed (and cached for ss_transmission).
+ * G_1n is computed (and T cached for ss_transmission), keeping the corner
+ * blocks of the inverse instead of its block columns (transmission-only mode).
  * 1 <= n_inj <= cfg.max_inj.  In the mixed modes x is refined in FP64 until
  * the normwise backward error ||Inj - (A - Sigma) x||_F /
  * (||A - Sigma||_F ||x||_F + ||Inj||_F) is <= ir_tol, until a correction no
@@ -137,6 +157,19 @@ int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id,
  * same points; otherwise runs the whole pipeline. */
 int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id,
                     double* T, double* err_est, int* status);
+
+/* Local density of states per block of the open system:
+ *   dos[p][i] = -Im Tr[G_ii] / pi,  G = (E S - H - Sigma_L (+) 0 (+) .. (+) Sigma_R)^-1,
+ * for every block i = 1..n_b of point p (the retarded Green's function of
+ * Eq. negf, whose diagonal gives the spectral weight the observables of
+ * Sec. 2B are integrated from).  dos: n_b doubles per point, packed.
+ * Computed by two block sweeps over A - Sigma (right- and left-connected
+ * Schur complements of every block) and one LU per block of
+ * (A_ii - Sigma^left_i - Sigma^right_i), Sigma from the doubling (cached when
+ * the points equal the previous call's).  Needs 2 n_b s_b^2 complex of block
+ * storage per point (ignores cfg.partitions).  status as in ss_self_energy,
+ * SS_ERR_SINGULAR for a zero pivot in any block. */
+int ss_dos(ss_handle* h, int n_pts, const double* E, const int* k_id, double* dos, int* status);
 
 /* Release every device allocation of the handle (NULL is accepted). */
 int ss_destroy(ss_handle* h);
@@ -252,6 +285,12 @@ int ss_mlp_forward(ss_mlp* net, int B, const float* x, float* y);
  * be NULL) receives the loss of this batch (the call then synchronises). */
 int ss_mlp_train_step(ss_mlp* net, int B, const float* x, const float* t, float lr, double* loss);
 const char* ss_mlp_last_error(const ss_mlp* net);
+
+/* Transverse momentum k of Hamiltonian k_id (default 0): the value the
+ * warm-start network is fed for this k_id inside the pipeline
+ * (cfg.warm_start).  Errors: SS_ERR_STATE (no Hamiltonian for k_id),
+ * SS_ERR_ARG (non-finite k). */
+int ss_set_momentum(ss_handle* h, int k_id, double k);
 
 /* Attach a trained network as the warm start of lead `side` (0 left, 1 right)
  * for k-points with block size s_b = sqrt(n_out / 2); the network is not

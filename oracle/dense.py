@@ -127,3 +127,18 @@ def backward_error(M, x, b):
 def rel_T_err(T, T_ref):
     """|T - T_ref| / max(1, |T_ref|): a relative error that stays defined in gaps."""
     return abs(T - T_ref) / max(1.0, abs(T_ref))
+
+
+def ldos(dev, E, eta=leads.DEFAULT_ETA, tol=leads.DEFAULT_TOL, max_iter=leads.DEFAULT_MAX_ITER, sigmas=None):
+    """Local density of states per block, rho_i = -Im Tr[G_ii] / pi, from the
+    dense inverse G = (E S - H - Sigma)^-1 of the open system (Eq. negf: G^R is
+    the inverse of the boundary-corrected matrix of Eq. wf).  The blocks' traces
+    are the spectral weight the paper's observables (charge and current
+    densities, Sec. 2B) are integrated from.  Returns an array of n_b values."""
+    n, s = dev.n_b, dev.s_b
+    if sigmas is None:
+        sL, sR, _ = leads.self_energies(dev, E, eta, tol, max_iter)
+    else:
+        sL, sR = sigmas
+    G = np.linalg.inv(system_matrix(dev, E, sL, sR))
+    return np.array([-np.trace(G[i * s:(i + 1) * s, i * s:(i + 1) * s]).imag / np.pi for i in range(n)])

@@ -31,7 +31,8 @@ EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_ener
            "ss_profile_reset", "ss_profile_read_issued", "ss_zgemm", "ss_caroli_transmission",
            "ss_caroli_transmission_noalloc", "ss_noalloc_last_error", "ss_mlp_create", "ss_mlp_destroy",
            "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward", "ss_mlp_train_step", "ss_mlp_last_error",
-           "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan")
+           "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan", "ss_dos",
+           "ss_set_momentum")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
                 "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
                 "oz_scale": 13, "oz_pack": 14, "ozgemm": 15, "frob2": 16, "zgemm_lu": 17, "ozgemm_lu": 18}
@@ -43,7 +44,7 @@ class SSConfig(C.Structure):
         ("precision", C.c_int), ("eta", C.c_double), ("decim_tol", C.c_double),
         ("decim_max_iter", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
         ("warm_start", C.c_int), ("stream", C.c_void_p), ("device_ptrs", C.c_int),
-        ("use_graphs", C.c_int), ("profile", C.c_int),
+        ("use_graphs", C.c_int), ("profile", C.c_int), ("partitions", C.c_int), ("memory_lean", C.c_int),
     ]
 
 
@@ -72,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     lib.ss_self_energy.argtypes = [vp, C.c_int, dp, ip, vp, vp, ip, ip]
     lib.ss_solve.argtypes = [vp, C.c_int, dp, ip, C.c_int, vp, vp, ip]
     lib.ss_transmission.argtypes = [vp, C.c_int, dp, ip, vp, vp, ip]
+    lib.ss_dos.argtypes = [vp, C.c_int, dp, ip, vp, ip]
+    lib.ss_dos.restype = C.c_int
     lib.ss_destroy.argtypes = [vp]
     lib.ss_last_error.argtypes = [vp]
     lib.ss_last_error.restype = C.c_char_p
@@ -102,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.ss_mlp_last_error.argtypes = [vp]
     lib.ss_mlp_last_error.restype = C.c_char_p
     lib.ss_set_warm_start.argtypes = [vp, vp, C.c_int, C.c_double]
+    lib.ss_set_momentum.argtypes = [vp, C.c_int, C.c_double]
+    lib.ss_set_momentum.restype = C.c_int
     lib.ss_autotune.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, ip, ip, ip, dp]
     lib.ss_autotune.restype = C.c_int
     ub = C.POINTER(C.c_ubyte)
@@ -308,6 +313,10 @@ class Handle:
                                           C.byref(upd), C.byref(ms)))
         return nb.value, nbo.value, upd.value, ms.value
 
+    def set_momentum(self, k_id, k):
+        """ss_set_momentum: transverse momentum of k_id fed to the warm-start network."""
+        self._check(self._lib.ss_set_momentum(self._h, int(k_id), float(k)))
+
     def set_warm_start(self, net, side, out_scale):
         """ss_set_warm_start: attach a trained MLP to lead `side` (0 left, 1 right)."""
         self._check(self._lib.ss_set_warm_start(self._h, net._n, int(side), float(out_scale)))
@@ -333,6 +342,25 @@ class Handle:
                                      st.ctypes.data_as(C.POINTER(C.c_int)))
         self._check(rc, allow)
         return self._split(g, k), it, sd, st, rc
+
+    def dos(self, E, k_id, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
+        """ss_dos: local density of states -Im Tr[G_ii]/pi per block.
+
+        Returns (list of (n_b,) arrays, status (P,), rc)."""
+        E, k = self._pts(E, k_id)
+        P = E.size
+        tot = int(sum(self.shapes[int(q)][0] for q in k))
+        out = self._alloc(tot, np.float64)
+        st = np.zeros(P, np.int32)
+        rc = self._lib.ss_dos(self._h, P, E.ctypes.data_as(C.POINTER(C.c_double)),
+                              k.ctypes.data_as(C.POINTER(C.c_int)), _ptr(out), st.ctypes.data_as(C.POINTER(C.c_int)))
+        self._check(rc, allow)
+        res, o = [], 0
+        for q in k:
+            n = self.shapes[int(q)][0]
+            res.append(out[o:o + n])
+            o += n
+        return res, st, rc
 
     def transmission(self, E, k_id, allow=(SS_ERR_NOT_CONVERGED, SS_ERR_SINGULAR)):
         """Returns (T (P,), err_est (P,), status (P,), rc)."""

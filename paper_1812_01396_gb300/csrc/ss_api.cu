@@ -45,11 +45,17 @@ constexpr int LU_NB = 0;  // panel width chosen per group from its largest block
 // tensor-core trailing updates then have depth 128 instead of the panel width.
 inline int lu_outer_default(int smax) { return smax >= 256 ? 128 : (smax >= 128 ? 64 : 0); }
 constexpr int MAX_K_ID = 4096;
+// Learned warm start inside the pipeline: fixed-point steps after the network's
+// seed and the Dyson-residual acceptance threshold (cap 8 steps, accept at
+// ||g (D - U g L) - 1||_F / sqrt(s) <= 1e-10; doubling otherwise).
+constexpr int WARM_ITERS = 8;
+constexpr double WARM_TOL = 1e-10;
 
 std::string g_create_error;
 
 struct KData {
   int n = 0, s = 0;
+  double kval = 0.0;  // transverse momentum fed to the warm-start network
   z64 *Hd = nullptr, *Hu = nullptr, *Sd = nullptr, *Su = nullptr, *lead = nullptr;
   // lead cells: [side][0..3] = H00, H01, S00, S01
   const z64* cell[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
@@ -72,33 +78,72 @@ struct Carve {
   }
 };
 
+// Most partitions a device is split into (Sec. 3B, Fig. pp).
+constexpr int MAXP = 8;
+// Blocks per point whose diagonal Green's function blocks one round of the
+// density-of-states step inverts.
+constexpr int DOS_ROUND = 8;
+
+// What the sweeps of a call must keep.
+enum Layout {
+  LAYOUT_FULL = 0,  // both block columns of every partition (wave functions x)
+  LAYOUT_LEAN = 1,  // transmission only: running corner products, no block columns
+  LAYOUT_DOS = 2    // density of states: the two sweeps' Schur products of every block
+};
+
 // Workspace of one point inside a chunk.
 struct PW {
   int idx = 0;  // position in the call's arrays
   int n = 0, s = 0;
   double E = 0.0;
   const KData* kd = nullptr;
+  // partitions: np contiguous block ranges [pa[j], pb[j]] (1-based), whose
+  // sweeps run concurrently and are merged by one SMW system of 2 np s rows
+  int np = 1;
+  int pa[MAXP] = {0}, pb[MAXP] = {0};
+  Layout layout = LAYOUT_FULL;
   // self-energy doubling, side 0 = left lead, 1 = right lead
   z64 *D[2], *e[2], *es[2], *a[2][2], *b[2][2], *T1[2], *T2[2], *Wd[2];
   int* ipd[2];
   z64* sig[2];
-  // sweeps, dir 0 = first block column, 1 = last block column
-  z64 *X[2], *Ws[2], *tmp[2];
-  int* ips[2];
+  // sweeps, dir 0 = first block column, 1 = last block column of each partition
+  z64* X[2] = {nullptr, nullptr};  // full: the block columns (global block index); dos: Schur products
+  z64* Ws[MAXP][2];                // [D_i | RHS (| 1)] work of each sweep
+  int* ips[MAXP][2];
+  z64* tmp[MAXP][2];               // full: chain product
+  z64* Xl[MAXP][2][2];             // lean, dos: ping-pong X_i of the sweep
+  z64* Rl[MAXP][2][2];             // lean: ping-pong running corner product
+  const z64* Gc[MAXP][4];          // corners of each partition's inverse: G_aa, G_ba, G_ab, G_bb
   // boundary
   z64 *Rw, *gb, *cv, *G1n, *Gam[2], *M1, *M2;
   int* ipr;
-  z64* inj;  // device copy or user pointer (2s x ninj)
-  z64* x;    // device output (N x ninj)
+  z64* inj = nullptr;  // device copy or user pointer (2s x ninj)
+  z64* x = nullptr;    // device output (N x ninj)
   // FP64 iterative refinement of x (mixed mode): D_i^-1 of the first-column
   // sweep, R^-1, residual r, UL-substitution work w, SMW work zc, t
   z64 *Dinv = nullptr, *r = nullptr, *wv = nullptr, *zc = nullptr, *tv = nullptr;
+  // density of states: [K_i | 1] of one round of blocks, pivots
+  z64* Kw = nullptr;
+  int* ipk = nullptr;
+  int rows() const { return 2 * np * s; }  // rows of the boundary system
 };
 
-// Workspace of one point; with `ir` also the refinement buffers.  The layout
-// depends only on (n, s, ninj, ir), so cached results keep their addresses.
-void carve_point(Carve& c, PW& w, int ninj, bool ir = false) {
-  const int n = w.n, s = w.s;
+// Split n blocks into np contiguous partitions of (almost) equal length.
+void set_partitions(PW& w, int parts) {
+  w.np = std::max(1, std::min({parts, w.n, MAXP}));
+  for (int j = 0; j < w.np; ++j) {
+    w.pa[j] = 1 + (int)((long long)j * w.n / w.np);
+    w.pb[j] = (int)((long long)(j + 1) * w.n / w.np);
+  }
+}
+
+// Workspace of one point, in two parts.  The doubling buffers and the
+// self-energies of every point of a batch are carved first (carve_doubling),
+// so their addresses depend only on the batch's block sizes and cached
+// self-energies stay valid whatever the next call's layout, partitions or
+// n_inj; the sweep and boundary buffers follow (carve_sweeps).
+void carve_doubling(Carve& c, PW& w) {
+  const int s = w.s;
   const size_t ss2 = (size_t)s * s;
   for (int q = 0; q < 2; ++q) {
     w.D[q] = c.take<z64>(ss2); w.e[q] = c.take<z64>(ss2); w.es[q] = c.take<z64>(ss2);
@@ -107,31 +152,64 @@ void carve_point(Carve& c, PW& w, int ninj, bool ir = false) {
     w.T1[q] = c.take<z64>(ss2); w.T2[q] = c.take<z64>(ss2); w.Wd[q] = c.take<z64>(3 * ss2);
     w.ipd[q] = c.take<int>(s);
     w.sig[q] = c.take<z64>(ss2);
-    w.X[q] = c.take<z64>((size_t)n * ss2); w.Ws[q] = c.take<z64>(3 * ss2); w.tmp[q] = c.take<z64>(ss2);
-    w.ips[q] = c.take<int>(s);
-  }
-  const int ldr = 3 * s + ninj + (ir ? 2 * s : 0);
-  w.Rw = c.take<z64>((size_t)2 * s * ldr); w.gb = c.take<z64>((size_t)2 * s * ninj);
-  w.cv = c.take<z64>((size_t)2 * s * ninj); w.G1n = c.take<z64>(ss2);
-  w.Gam[0] = c.take<z64>(ss2); w.Gam[1] = c.take<z64>(ss2); w.M1 = c.take<z64>(ss2); w.M2 = c.take<z64>(ss2);
-  w.ipr = c.take<int>(2 * s);
-  w.inj = c.take<z64>((size_t)2 * s * ninj);
-  w.x = c.take<z64>((size_t)n * s * ninj);
-  if (ir) {
-    w.Dinv = c.take<z64>((size_t)n * ss2);
-    w.r = c.take<z64>((size_t)n * s * ninj);
-    w.wv = c.take<z64>((size_t)n * s * ninj);
-    w.zc = c.take<z64>((size_t)2 * s * ninj);
-    w.tv = c.take<z64>((size_t)2 * s * ninj);
   }
 }
 
-size_t point_bytes(int n, int s, int ninj, bool ir = false) {
+void carve_sweeps(Carve& c, PW& w, int ninj, bool ir) {
+  const int n = w.n, s = w.s;
+  const size_t ss2 = (size_t)s * s;
+  const Layout L = w.layout;
+  if (L != LAYOUT_LEAN) { w.X[0] = c.take<z64>((size_t)n * ss2); w.X[1] = c.take<z64>((size_t)n * ss2); }
+  for (int j = 0; j < w.np; ++j)
+    for (int d = 0; d < 2; ++d) {
+      w.Ws[j][d] = c.take<z64>(3 * ss2);
+      w.ips[j][d] = c.take<int>(s);
+      if (L == LAYOUT_FULL) w.tmp[j][d] = c.take<z64>(ss2);
+      if (L != LAYOUT_FULL) { w.Xl[j][d][0] = c.take<z64>(ss2); w.Xl[j][d][1] = c.take<z64>(ss2); }
+      if (L == LAYOUT_LEAN) { w.Rl[j][d][0] = c.take<z64>(ss2); w.Rl[j][d][1] = c.take<z64>(ss2); }
+    }
+  if (L == LAYOUT_DOS) {
+    const int rb = std::min(n, DOS_ROUND);
+    w.Kw = c.take<z64>((size_t)rb * 2 * ss2);
+    w.ipk = c.take<int>((size_t)rb * s);
+    return;
+  }
+  const int S2 = w.rows();
+  const int nj = L == LAYOUT_FULL ? ninj : 0;
+  const bool irr = ir && L == LAYOUT_FULL;
+  const int ldr = S2 + s + nj + (irr ? S2 : 0);
+  w.Rw = c.take<z64>((size_t)S2 * ldr);
+  w.G1n = c.take<z64>(ss2);
+  w.Gam[0] = c.take<z64>(ss2); w.Gam[1] = c.take<z64>(ss2); w.M1 = c.take<z64>(ss2); w.M2 = c.take<z64>(ss2);
+  w.ipr = c.take<int>(S2);
+  if (L == LAYOUT_FULL) {
+    w.gb = c.take<z64>((size_t)S2 * ninj);
+    w.cv = c.take<z64>((size_t)S2 * ninj);
+    w.inj = c.take<z64>((size_t)2 * s * ninj);
+    w.x = c.take<z64>((size_t)n * s * ninj);
+  }
+  if (irr) {
+    w.Dinv = c.take<z64>((size_t)n * ss2);
+    w.r = c.take<z64>((size_t)n * s * ninj);
+    w.wv = c.take<z64>((size_t)n * s * ninj);
+    w.zc = c.take<z64>((size_t)S2 * ninj);
+    w.tv = c.take<z64>((size_t)S2 * ninj);
+  }
+}
+
+// Carve a batch: every point's doubling part, then every point's sweep part.
+void carve_batch(Carve& c, std::vector<PW>& pts, int ninj, bool ir) {
+  for (auto& w : pts) carve_doubling(c, w);
+  for (auto& w : pts) carve_sweeps(c, w, ninj, ir);
+}
+
+size_t point_bytes(int n, int s, int ninj, bool ir, Layout layout, int parts) {
   Carve c(nullptr);
-  PW w;
-  w.n = n; w.s = s;
-  carve_point(c, w, ninj, ir);
-  return c.off + 256;
+  std::vector<PW> one(1);
+  one[0].n = n; one[0].s = s; one[0].layout = layout;
+  set_partitions(one[0], parts);
+  carve_batch(c, one, ninj, ir);
+  return c.off + 512;
 }
 
 // ------------------------------------------------------------ descriptors
@@ -265,11 +343,17 @@ void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
 
 // ---------------------------------------------------------- self-energies
 // Builds setup / iteration / final plans for the doubling of 2P lead problems.
+// seeded (optional, 2 per point): 1 where an accepted warm start already holds
+// the lead's surface Green's function g in es[q]; that lead skips the doubling
+// (its flag starts at 0) and its self-energy is A_{1,0} g A_{0,1} (left) or
+// A_{n,n+1} g A_{n+1,n} (right).
 void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, int* conv,
-                      int* info, double* na, double* nb, double* nd, bool preset_act = false) {
+                      int* info, double* na, double* nb, double* nd, bool preset_act = false,
+                      const std::vector<int>* seeded = nullptr) {
   const int P = (int)pts.size();
   const int NP = 2 * P;
   const double eta = h->cfg.eta;
+  auto is_seeded = [&](int i) { return seeded && (*seeded)[i] != 0; };
   Plan& S = h->p_setup;
   S.clear();
   std::vector<FormDesc> f;
@@ -279,6 +363,7 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
     const int s = w.s;
     const z64 z = make_double2(w.E, eta);
     for (int q = 0; q < 2; ++q) {
+      if (is_seeded(2 * p + q)) continue;
       const z64* const* c = w.kd->cell[q];
       f.push_back(fformed(w.D[q], s, c[2], c[0], z, s, s, s));
       f.push_back(fformed(w.e[q], s, c[2], c[0], z, s, s, s));
@@ -300,6 +385,7 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
     PW& w = pts[p];
     for (int q = 0; q < 2; ++q) {
       const int i = 2 * p + q;
+      if (is_seeded(i)) continue;
       nD.push_back({w.D[q], w.s, w.s, w.s, nd + i, nullptr});
       nA.push_back({w.a[q][0], w.s, w.s, w.s, na + i, nullptr});
       nA.push_back({w.b[q][0], w.s, w.s, w.s, nb + i, nullptr});
@@ -366,6 +452,7 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
   std::vector<FormDesc> ff;
   std::vector<LuDesc> lu;
   std::vector<GemmDesc> g;
+  std::vector<GemmDesc> gs;
   for (int p = 0; p < P; ++p) {
     PW& w = pts[p];
     const int s = w.s, ld = 3 * s;
@@ -373,72 +460,243 @@ void build_decimation(ss_handle* h, std::vector<PW>& pts, int* act, int* iters, 
     for (int q = 0; q < 2; ++q) {
       const z64* const* c = w.kd->cell[q];
       z64* W = w.Wd[q];
-      ff.push_back(fcopy(W, ld, w.es[q], s, s, s));
-      // right: rhs A_{n+1,n} = (E S01 - H01)^H ; left: rhs A_{0,1} = E S01 - H01
-      ff.push_back(fformed(W + s, ld, c[3], c[1], E, s, s, s, q == 1 ? 1 : 0));
-      LuDesc L{};
-      L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[q]; L.info = info + NP + 2 * p + q;
-      lu.push_back(L);
+      if (is_seeded(2 * p + q)) {
+        // W + s = g A (seeded g), in place of the solve es W = A below
+        gs.push_back(gdesc(s, s, s, plain(w.es[q], s), formed(c[3], c[1], E, s, q == 1 ? 1 : 0), W + s, ld, ONE, ZERO));
+      } else {
+        ff.push_back(fcopy(W, ld, w.es[q], s, s, s));
+        // right: rhs A_{n+1,n} = (E S01 - H01)^H ; left: rhs A_{0,1} = E S01 - H01
+        ff.push_back(fformed(W + s, ld, c[3], c[1], E, s, s, s, q == 1 ? 1 : 0));
+        LuDesc L{};
+        L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[q]; L.info = info + NP + 2 * p + q;
+        lu.push_back(L);
+      }
       g.push_back(gdesc(s, s, s, formed(c[3], c[1], E, s, q == 1 ? 0 : 1), plain(W + s, ld), w.sig[q], s,
                         ONE, ZERO));
     }
   }
   F.form(ff);
   ::lu(h, F, lu);
+  big_gemm(h, F, gs);
   big_gemm(h, F, g);
 }
 
+// Warm start of lead `side` for the points of one batch (all of block size
+// s = sqrt(n_out / 2) of the attached network): network seed g0 = MLP(E, k),
+// at most `iters` steps of g <- (D - U g L)^-1 (right lead; (D - L g U)^-1
+// left), then the FP64 Dyson residual ||g (D - U g L) - 1||_F / sqrt(s); a
+// point is accepted when it is <= tol, with g left in es[side].
+// Returns SS_OK or a call-level error; accepted[p] on the host.
+int warm_seed(ss_handle* h, std::vector<PW>& pts, int side, const std::vector<double>& kvals, int iters,
+              double tol, int* dinfo, std::vector<int>& accepted) {
+  ss_mlp* net = h->warm_net[side];
+  const int P = (int)pts.size();
+  accepted.assign(P, 0);
+  if (!net || P == 0) return SS_OK;
+  int n_in = 0, n_out = 0, mb = 0;
+  mlp_dims(net, &n_in, &n_out, &mb);
+  const int s = pts[0].s;
+  for (auto& w : pts)
+    if (w.s != s || 2 * s * s != n_out) return fail(h, SS_ERR_ARG, "network output does not match s_b");
+  if (P > mb) return fail(h, SS_ERR_ARG, "network max_batch below max_points");
+  cudaStream_t st = h->stream;
+  const double eta = h->cfg.eta;
+  const int P_max = h->cfg.max_points;
+  const size_t need = (size_t)P_max * (n_in + n_out);
+  if (need > h->warm_cap) {
+    cudaFree(h->feat); cudaFree(h->warm_y); cudaFree(h->wres);
+    h->feat = nullptr; h->warm_y = nullptr; h->wres = nullptr;
+    CK(cudaMalloc(&h->feat, (size_t)P_max * n_in * sizeof(float)), "warm features");
+    CK(cudaMalloc(&h->warm_y, (size_t)P_max * n_out * sizeof(float)), "warm outputs");
+    CK(cudaMalloc(&h->wres, (size_t)P_max * sizeof(double)), "warm residuals");
+    h->warm_cap = need;
+  }
+  std::vector<float> f((size_t)P * n_in, 0.f);
+  for (int p = 0; p < P; ++p) {
+    const double e = pts[p].E, k = kvals[p];
+    float* r = &f[(size_t)p * n_in];
+    r[0] = (float)e; r[1] = (float)std::cos(k); r[2] = (float)std::sin(k);
+    for (int m = 1; m <= 8 && 3 + 2 * m - 1 < n_in; ++m) {
+      r[3 + 2 * (m - 1)] = (float)std::sin(m * M_PI * e);
+      r[4 + 2 * (m - 1)] = (float)std::cos(m * M_PI * e);
+    }
+  }
+  cudaStream_t ns = mlp_stream(net);
+  CK(cudaMemcpyAsync(h->feat, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, ns), "features");
+  int r2 = ss_mlp_forward(net, P, h->feat, h->warm_y);
+  if (r2 != SS_OK) return fail(h, r2, "network forward failed");
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  cudaEventRecord(ev, ns);
+  cudaStreamWaitEvent(st, ev, 0);
+  cudaEventDestroy(ev);
+  for (int p = 0; p < P; ++p) {
+    launch_unpack_g(h->warm_y + (size_t)p * n_out, s, 1.0 / h->warm_scale[side], pts[p].es[side], s, st);
+    ++h->nlaunch;
+  }
+  // lead blocks at z and one fixed-point step g <- (D - U g L)^-1 (right) / (D - L g U)^-1 (left)
+  Plan& setup = h->p_setup;
+  setup.clear();
+  std::vector<FormDesc> fl;
+  for (auto& w : pts) {
+    const z64 z = make_double2(w.E, eta);
+    const z64* const* cc = w.kd->cell[side];
+    fl.push_back(fformed(w.D[side], s, cc[2], cc[0], z, s, s, s));
+    fl.push_back(fformed(w.a[side][0], s, cc[3], cc[1], z, s, s, s));
+    fl.push_back(fformed(w.b[side][0], s, cc[3], cc[1], z, s, s, s, 1));
+  }
+  setup.form(fl);
+  Plan& I = h->p_warm_iter;
+  I.clear();
+  std::vector<GemmDesc> g1, g2;
+  std::vector<FormDesc> f1, f2;
+  std::vector<LuDesc> lus;
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
+    const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
+    z64* W = w.Wd[side];
+    g1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
+    f1.push_back(fcopy(W, 2 * s, w.D[side], s, s, s));
+    f1.push_back(fident(W + s, 2 * s, s, s, 1.0));
+    g2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, 2 * s, MONE, ONE));
+    LuDesc L{};
+    L.w = W; L.ldw = 2 * s; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[side]; L.info = dinfo + 2 * p + side;
+    lus.push_back(L);
+    f2.push_back(fcopy(w.es[side], s, W + s, 2 * s, s, s));
+  }
+  I.memset0(dinfo, sizeof(int) * 4 * P);
+  big_gemm(h, I, g1);
+  I.form(f1);
+  big_gemm(h, I, g2);
+  ::lu(h, I, lus);
+  I.form(f2);
+  // judge: ||g (D - U g L) - 1||_F^2 into wres, in FP64 whatever the precision mode
+  Plan& J = h->p_warm_judge;
+  J.clear();
+  std::vector<GemmDesc> j1, j2, j3;
+  std::vector<FormDesc> jf;
+  std::vector<Norm1Desc> fr;
+  J.memset0(h->wres, sizeof(double) * P);
+  for (int p = 0; p < P; ++p) {
+    PW& w = pts[p];
+    const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
+    const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
+    z64* W = w.Wd[side];
+    j1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
+    jf.push_back(fcopy(W, s, w.D[side], s, s, s));
+    j2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, s, MONE, ONE));
+    GemmDesc q = gdesc(s, s, s, plain(w.es[side], s), plain(W, s), w.T2[side], s, ONE, MONE);
+    q.cmode = 2;
+    j3.push_back(q);
+    fr.push_back({w.T2[side], s, s, s, h->wres + p, nullptr});
+  }
+  J.gemm(j1);
+  J.form(jf);
+  J.gemm(j2);
+  J.gemm(j3);
+  J.frob2(fr);
+  if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small");
+  CK(setup.upload(st), "upload warm");
+  CK(I.upload(st), "upload warm");
+  CK(J.upload(st), "upload warm");
+  CK(setup.run(st, &h->nlaunch, h->P()), "warm setup");
+  for (int it = 0; it < iters; ++it) CK(I.run(st, &h->nlaunch, h->P()), "warm step");
+  CK(J.run(st, &h->nlaunch, h->P()), "warm judge");
+  std::vector<double> res(P);
+  std::vector<int> info(2 * P);
+  CK(cudaMemcpyAsync(res.data(), h->wres, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read residual");
+  CK(cudaMemcpyAsync(info.data(), dinfo, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read info");
+  CK(cudaStreamSynchronize(st), "warm sync");
+  for (int p = 0; p < P; ++p)
+    accepted[p] = (std::isfinite(res[p]) && std::sqrt(res[p] / (double)s) <= tol && info[2 * p + side] == 0) ? 1 : 0;
+  return SS_OK;
+}
+
 // ------------------------------------------------------------------ sweeps
-void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
+// Longest partition of the chunk: the number of sequential sweep steps.
+int sweep_steps(const std::vector<PW>& pts) {
+  int m = 0;
+  for (auto& w : pts)
+    for (int j = 0; j < w.np; ++j) m = std::max(m, w.pb[j] - w.pa[j] + 1);
+  return m;
+}
+size_t sinfo_index(int p, int j, int dir, int t, int nsteps) {
+  return ((size_t)(p * MAXP + j) * 2 + dir) * nsteps + t;
+}
+
+// Algorithm 1 (first block column) and its mirror (last block column) of the
+// inverse of every partition A_j = A[a..b, a..b] of every point, all in the same
+// launches (Sec. 3B: the two columns, and the partitions, are independent).
+// Inside a partition the neighbours outside it do not exist: A_{a,a-1} := 1
+// for the first column, A_{b,b+1} := 1 for the last.
+//   full layout: X_i is stored, then the chains Q_i = -X_i Q_{i-1} overwrite it;
+//   lean layout: only the corners are kept.  G_aa = X_a is the sweep's last
+//     X, and G_ba = Q_b = (-1)^(L-1) X_b X_{b-1} ... X_a is accumulated while
+//     the sweep runs (R <- -R X_i, one product per block as in the chain, but
+//     in the next step's launch and with no block column in memory); the
+//     mirror gives G_bb and G_ab the same way.
+// with_inv: the first-column sweep also returns D_i^-1 (refinement of x).
+void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nsteps, bool with_inv) {
   Plan& S = h->p_sweep;
   S.clear();
   const int P = (int)pts.size();
-  const bool ir = h->mixed();  // first-column sweep also returns D_i^-1 for the refinement
-  S.memset0(info, sizeof(int) * 2 * P * nmax);
-  for (int t = 0; t < nmax; ++t) {
+  S.memset0(info, sizeof(int) * 2 * MAXP * (size_t)P * nsteps);
+  for (int t = 0; t <= nsteps; ++t) {  // t = nsteps: the lean layout's last running products
     std::vector<GemmDesc> g;
     std::vector<FormDesc> f, fc;
     std::vector<LuDesc> lu;
     for (int p = 0; p < P; ++p) {
       PW& w = pts[p];
-      const int n = w.n, s = w.s;
-      if (t >= n) continue;
+      const int s = w.s;
       const KData* kd = w.kd;
       const size_t ss2 = (size_t)s * s;
       const z64 E = make_double2(w.E, 0.0);
-      for (int dir = 0; dir < 2; ++dir) {
-        const int i = dir == 0 ? n - t : t + 1;  // 1-based block
-        const bool with_inv = ir && dir == 0;
-        const int ld = with_inv ? 3 * s : 2 * s;
-        z64* W = w.Ws[dir];
-        const z64* Sii = kd->Sd + (i - 1) * ss2;
-        const z64* Hii = kd->Hd + (i - 1) * ss2;
-        if (t == 0) {
-          f.push_back(fformed(W, ld, Sii, Hii, E, s, s, s));
-        } else {
-          // D_i = A_ii - A_{i,i+1} X_{i+1} (first) or A_ii - A_{i,i-1} Y_{i-1} (last)
-          const int up = dir == 0 ? i - 1 : i - 2;  // 0-based upper block index
-          const int prev = dir == 0 ? i + 1 : i - 1;
-          GemmDesc q = gdesc(s, s, s, formed(kd->Su + up * ss2, kd->Hu + up * ss2, E, s, dir == 0 ? 0 : 1),
-                             plain(w.X[dir] + (prev - 1) * ss2, s), W, ld, MONE, ONE);
-          q.cmode = 1; q.cs = Sii; q.ch = Hii; q.ce = E; q.ldcf = s;
-          g.push_back(q);
+      const bool lean = w.layout == LAYOUT_LEAN;
+      for (int j = 0; j < w.np; ++j) {
+        const int a = w.pa[j], b = w.pb[j], len = b - a + 1;
+        for (int dir = 0; dir < 2; ++dir) {
+          if (lean && t >= 2 && t <= len) {
+            // running corner product of step t-1: R_{t-1} = -R_{t-2} X_{t-1} (R_0 = X_0)
+            const z64* Rp = (t == 2) ? w.Xl[j][dir][0] : w.Rl[j][dir][t & 1];
+            g.push_back(gdesc(s, s, s, plain(Rp, s), plain(w.Xl[j][dir][(t - 1) & 1], s), w.Rl[j][dir][(t - 1) & 1],
+                              s, MONE, ZERO));
+          }
+          if (t >= len) continue;
+          const int i = dir == 0 ? b - t : a + t;  // 1-based block
+          const bool inv = with_inv && dir == 0;
+          const int ld = inv ? 3 * s : 2 * s;
+          z64* W = w.Ws[j][dir];
+          const z64* Sii = kd->Sd + (i - 1) * ss2;
+          const z64* Hii = kd->Hd + (i - 1) * ss2;
+          if (t == 0) {
+            f.push_back(fformed(W, ld, Sii, Hii, E, s, s, s));
+          } else {
+            // D_i = A_ii - A_{i,i+1} X_{i+1} (first) or A_ii - A_{i,i-1} Y_{i-1} (last)
+            const int up = dir == 0 ? i - 1 : i - 2;  // 0-based upper block index
+            const z64* Xp = lean ? w.Xl[j][dir][(t - 1) & 1] : w.X[dir] + (size_t)(dir == 0 ? i : i - 2) * ss2;
+            GemmDesc q = gdesc(s, s, s, formed(kd->Su + up * ss2, kd->Hu + up * ss2, E, s, dir == 0 ? 0 : 1),
+                               plain(Xp, s), W, ld, MONE, ONE);
+            q.cmode = 1; q.cs = Sii; q.ch = Hii; q.ce = E; q.ldcf = s;
+            g.push_back(q);
+          }
+          // right-hand side: A_{i,i-1} (first, 1 at i = a) / A_{i,i+1} (last, 1 at i = b)
+          if (dir == 0) {
+            if (i > a) f.push_back(fformed(W + s, ld, kd->Su + (i - 2) * ss2, kd->Hu + (i - 2) * ss2, E, s, s, s, 1));
+            else f.push_back(fident(W + s, ld, s, s, 1.0));
+          } else {
+            if (i < b) f.push_back(fformed(W + s, ld, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s, 0));
+            else f.push_back(fident(W + s, ld, s, s, 1.0));
+          }
+          if (inv) f.push_back(fident(W + 2 * s, ld, s, s, 1.0));
+          LuDesc L{};
+          L.w = W; L.ldw = ld; L.s = s; L.ncols = inv ? 3 * s : 2 * s; L.ipiv = w.ips[j][dir];
+          L.info = info + sinfo_index(p, j, dir, t, nsteps);
+          lu.push_back(L);
+          z64* Xo = lean ? w.Xl[j][dir][t & 1] : w.X[dir] + (size_t)(i - 1) * ss2;
+          fc.push_back(fcopy(Xo, s, W + s, ld, s, s));
+          if (inv) fc.push_back(fcopy(w.Dinv + (size_t)(i - 1) * ss2, s, W + 2 * s, ld, s, s));
         }
-        // right-hand side: A_{i,i-1} (first, I at i = 1) / A_{i,i+1} (last, I at i = n)
-        if (dir == 0) {
-          if (i > 1) f.push_back(fformed(W + s, ld, kd->Su + (i - 2) * ss2, kd->Hu + (i - 2) * ss2, E, s, s, s, 1));
-          else f.push_back(fident(W + s, ld, s, s, 1.0));
-        } else {
-          if (i < n) f.push_back(fformed(W + s, ld, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s, 0));
-          else f.push_back(fident(W + s, ld, s, s, 1.0));
-        }
-        if (with_inv) f.push_back(fident(W + 2 * s, ld, s, s, 1.0));
-        LuDesc L{};
-        L.w = W; L.ldw = ld; L.s = s; L.ncols = with_inv ? 3 * s : 2 * s; L.ipiv = w.ips[dir];
-        L.info = info + (size_t)(2 * p + dir) * nmax + t;
-        lu.push_back(L);
-        fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, W + s, ld, s, s));
-        if (with_inv) fc.push_back(fcopy(w.Dinv + (i - 1) * ss2, s, W + 2 * s, ld, s, s));
       }
     }
     big_gemm(h, S, g);
@@ -446,87 +704,156 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
     ::lu(h, S, lu);
     S.form(fc);
   }
-  // chains: Q_i = -X_i Q_{i-1} (first), P_i = -Y_i P_{i+1} (last)
-  for (int t = 1; t < nmax; ++t) {
+  for (auto& w : pts) {
+    if (w.layout != LAYOUT_LEAN) continue;
+    for (int j = 0; j < w.np; ++j) {
+      const int len = w.pb[j] - w.pa[j] + 1;
+      const int last = (len - 1) & 1;
+      w.Gc[j][0] = w.Xl[j][0][last];                              // G_aa = X_a
+      w.Gc[j][1] = len == 1 ? w.Xl[j][0][0] : w.Rl[j][0][last];   // G_ba
+      w.Gc[j][2] = len == 1 ? w.Xl[j][1][0] : w.Rl[j][1][last];   // G_ab
+      w.Gc[j][3] = w.Xl[j][1][last];                              // G_bb = Y_b
+    }
+  }
+  // full layout: chains Q_i = -X_i Q_{i-1} (first), P_i = -Y_i P_{i+1} (last)
+  for (int t = 1; t < nsteps; ++t) {
     std::vector<GemmDesc> g;
     std::vector<FormDesc> fc;
-    for (int p = 0; p < P; ++p) {
-      PW& w = pts[p];
-      const int n = w.n, s = w.s;
-      if (t >= n) continue;
+    for (auto& w : pts) {
+      if (w.layout != LAYOUT_FULL) continue;
+      const int s = w.s;
       const size_t ss2 = (size_t)s * s;
-      for (int dir = 0; dir < 2; ++dir) {
-        const int i = dir == 0 ? t + 1 : n - t;
-        const int prev = dir == 0 ? i - 1 : i + 1;
-        g.push_back(gdesc(s, s, s, plain(w.X[dir] + (i - 1) * ss2, s), plain(w.X[dir] + (prev - 1) * ss2, s),
-                          w.tmp[dir], s, MONE, ZERO));
-        fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, w.tmp[dir], s, s, s));
+      for (int j = 0; j < w.np; ++j) {
+        const int a = w.pa[j], b = w.pb[j];
+        if (t > b - a) continue;
+        for (int dir = 0; dir < 2; ++dir) {
+          const int i = dir == 0 ? a + t : b - t;
+          const int prev = dir == 0 ? i - 1 : i + 1;
+          g.push_back(gdesc(s, s, s, plain(w.X[dir] + (i - 1) * ss2, s), plain(w.X[dir] + (prev - 1) * ss2, s),
+                            w.tmp[j][dir], s, MONE, ZERO));
+          fc.push_back(fcopy(w.X[dir] + (i - 1) * ss2, s, w.tmp[j][dir], s, s, s));
+        }
       }
     }
     big_gemm(h, S, g);
     S.form(fc);
   }
+  for (auto& w : pts) {
+    if (w.layout != LAYOUT_FULL) continue;
+    const size_t ss2 = (size_t)w.s * w.s;
+    for (int j = 0; j < w.np; ++j) {
+      w.Gc[j][0] = w.X[0] + (size_t)(w.pa[j] - 1) * ss2;
+      w.Gc[j][1] = w.X[0] + (size_t)(w.pb[j] - 1) * ss2;
+      w.Gc[j][2] = w.X[1] + (size_t)(w.pa[j] - 1) * ss2;
+      w.Gc[j][3] = w.X[1] + (size_t)(w.pb[j] - 1) * ss2;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- boundary
-void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64* traces) {
+// The merged boundary system of Eq. x.  With np partitions, A - Sigma =
+// blockdiag(A_1 .. A_np) + B K' B^T, where B selects the first and last block
+// of every partition ("slots" 2j and 2j+1 for partition j) and K' holds
+// -Sigma_L (slot 0), -Sigma_R (slot 2 np - 1) and the couplings A_{b_j,b_j+1}
+// between neighbouring partitions (slots 2j+1 -> 2j+2 and back); np = 1 is
+// SplitSolve's Sigma^RB = B C.  SMW then gives
+//   R = 1 + K' g (g = B^T Q: the corners of every partition's inverse),
+//   z = -R^-1 K' g b'',  x = Q (b'' + z),  (A - Sigma)^-1 B = Q R^-1,
+// so G_1n = (g R^-1)[slot 0, slot 2np-1] and the partitions are merged by one
+// 2 np s system (the SPIKE-style merge of Sec. 3B, Fig. pp, in one step).
+struct KTerm {
+  int t;       // slot partner of the row slot
+  Operand op;  // K'(r, t) = alpha op
+  z64 alpha;
+};
+KTerm kterm(const PW& w, int r) {
+  const int S = 2 * w.np;
+  const size_t ss2 = (size_t)w.s * w.s;
+  const z64 E = make_double2(w.E, 0.0);
+  if (r == 0) return {0, plain(w.sig[0], w.s), MONE};
+  if (r == S - 1) return {S - 1, plain(w.sig[1], w.s), MONE};
+  if (r & 1) {  // last block b_j of partition j couples to the first block of j+1
+    const int bj = w.pb[r / 2];
+    return {r + 1, formed(w.kd->Su + (bj - 1) * ss2, w.kd->Hu + (bj - 1) * ss2, E, w.s), ONE};
+  }
+  const int bj = w.pb[r / 2 - 1];  // first block a_j couples back to b_{j-1}
+  return {r - 1, formed(w.kd->Su + (bj - 1) * ss2, w.kd->Hu + (bj - 1) * ss2, E, w.s, 1), ONE};
+}
+inline z64 zneg(z64 a) { return make_double2(-a.x, -a.y); }
+// Leading dimension of the boundary system [R | E_last | z rhs | (R^-1 rhs)].
+inline int bound_ld(const PW& w, int nj, bool irr) { return w.rows() + w.s + nj + (irr ? w.rows() : 0); }
+
+void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64* traces, bool ir) {
   Plan& B = h->p_bound;
   B.clear();
   const int P = (int)pts.size();
   B.memset0(info, sizeof(int) * P);
   std::vector<FormDesc> f0, fc, fg;
-  std::vector<GemmDesc> gR, gb1, gb2, gsb, gG1, gG2, gx1, gx2, gM;
+  std::vector<GemmDesc> gR, gbA, gbB, gsb, gG1, gG2, gx1, gx2, gM;
   std::vector<LuDesc> lu;
   std::vector<TraceDesc> tr;
-  const bool ir = h->mixed() && ninj > 0;
   for (int p = 0; p < P; ++p) {
     PW& w = pts[p];
-    const int n = w.n, s = w.s, ld = 3 * s + ninj + (ir ? 2 * s : 0);
+    const int s = w.s, S2 = w.rows(), NS = 2 * w.np;
+    const int nj = w.layout == LAYOUT_FULL ? ninj : 0;
+    const bool irr = ir && nj > 0;
+    const int ld = bound_ld(w, nj, irr);
     const size_t ss2 = (size_t)s * s;
-    const z64* G11 = w.X[0];
-    const z64* Gn1 = w.X[0] + (size_t)(n - 1) * ss2;
-    const z64* G1n = w.X[1];
-    const z64* Gnn = w.X[1] + (size_t)(n - 1) * ss2;
     z64* R = w.Rw;
-    f0.push_back(fident(R + 2 * s, ld, s, s, 0.0));
-    f0.push_back(fident(R + (size_t)s * ld + 2 * s, ld, s, s, 1.0));
-    if (ir) f0.push_back(fident(R + 3 * s + ninj, ld, 2 * s, 2 * s, 1.0));  // R^-1 for the refinement
-    GemmDesc q;
-    q = gdesc(s, s, s, plain(w.sig[0], s), plain(G11, s), R, ld, MONE, ONE); q.cmode = 2; gR.push_back(q);
-    gR.push_back(gdesc(s, s, s, plain(w.sig[0], s), plain(G1n, s), R + s, ld, MONE, ZERO));
-    gR.push_back(gdesc(s, s, s, plain(w.sig[1], s), plain(Gn1, s), R + (size_t)s * ld, ld, MONE, ZERO));
-    q = gdesc(s, s, s, plain(w.sig[1], s), plain(Gnn, s), R + (size_t)s * ld + s, ld, MONE, ONE); q.cmode = 2;
-    gR.push_back(q);
-    if (ninj > 0) {
+    f0.push_back(fident(R, ld, S2, S2, 1.0));                              // R = 1
+    f0.push_back(fident(R + S2, ld, S2 - s, s, 0.0));                      // E_last = [0; ..; 0; 1]
+    f0.push_back(fident(R + (size_t)(S2 - s) * ld + S2, ld, s, s, 1.0));   // (disjoint rows: one launch)
+    if (nj > 0) f0.push_back(fident(R + S2 + s, ld, S2, nj, 0.0));         // z right-hand side
+    if (irr) f0.push_back(fident(R + S2 + s + nj, ld, S2, S2, 1.0));       // R^-1 for the refinement
+    // R += K' g: row slot r meets its partner t, whose partition holds two column slots
+    for (int r = 0; r < NS; ++r) {
+      const KTerm k = kterm(w, r);
+      const int jt = k.t / 2, ut = k.t % 2;
+      for (int v = 0; v < 2; ++v)
+        gR.push_back(gdesc(s, s, s, k.op, plain(w.Gc[jt][ut + 2 * v], s), R + (size_t)r * s * ld + (size_t)(2 * jt + v) * s,
+                           ld, k.alpha, ONE));
+    }
+    if (nj > 0) {
       const z64* b1 = w.inj;
-      const z64* bn = w.inj + (size_t)s * ninj;
-      gb1.push_back(gdesc(s, ninj, s, plain(G11, s), plain(b1, ninj), w.gb, ninj, ONE, ZERO));
-      gb1.push_back(gdesc(s, ninj, s, plain(Gn1, s), plain(b1, ninj), w.gb + (size_t)s * ninj, ninj, ONE, ZERO));
-      gb2.push_back(gdesc(s, ninj, s, plain(G1n, s), plain(bn, ninj), w.gb, ninj, ONE, ONE));
-      gb2.push_back(gdesc(s, ninj, s, plain(Gnn, s), plain(bn, ninj), w.gb + (size_t)s * ninj, ninj, ONE, ONE));
-      gsb.push_back(gdesc(s, ninj, s, plain(w.sig[0], s), plain(w.gb, ninj), R + 3 * s, ld, ONE, ZERO));
-      gsb.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.gb + (size_t)s * ninj, ninj),
-                          R + (size_t)s * ld + 3 * s, ld, ONE, ZERO));
-      // c = b' + z
-      FormDesc c1 = fcopy(w.cv, ninj, b1, ninj, s, ninj);
-      c1.y = R + 3 * s; c1.ldy = ld; c1.ay = ONE;
-      fc.push_back(c1);
-      FormDesc c2 = fcopy(w.cv + (size_t)s * ninj, ninj, bn, ninj, s, ninj);
-      c2.y = R + (size_t)s * ld + 3 * s; c2.ldy = ld; c2.ay = ONE;
-      fc.push_back(c2);
-      for (int i = 0; i < n; ++i) {
-        z64* xi = w.x + (size_t)i * s * ninj;
-        gx1.push_back(gdesc(s, ninj, s, plain(w.X[0] + i * ss2, s), plain(w.cv, ninj), xi, ninj, ONE, ZERO));
-        gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.cv + (size_t)s * ninj, ninj), xi,
-                            ninj, ONE, ONE));
+      const z64* bn = w.inj + (size_t)s * nj;
+      const int jl = w.np - 1;
+      // gb = g b'': b'_1 sits in slot 0 (partition 0), b'_n in slot NS - 1 (last partition)
+      for (int u = 0; u < 2; ++u) {
+        gbA.push_back(gdesc(s, nj, s, plain(w.Gc[0][u], s), plain(b1, nj), w.gb + (size_t)u * s * nj, nj, ONE, ZERO));
+        gbB.push_back(gdesc(s, nj, s, plain(w.Gc[jl][u + 2], s), plain(bn, nj), w.gb + (size_t)(2 * jl + u) * s * nj, nj,
+                            ONE, w.np == 1 ? ONE : ZERO));
       }
+      // z right-hand side -K'(r, t) gb(t), non-zero where t is a slot of the first or last partition
+      for (int r = 0; r < NS; ++r) {
+        const KTerm k = kterm(w, r);
+        const int jt = k.t / 2;
+        if (jt != 0 && jt != jl) continue;
+        gsb.push_back(gdesc(s, nj, s, k.op, plain(w.gb + (size_t)k.t * s * nj, nj), R + (size_t)r * s * ld + S2 + s, ld,
+                            zneg(k.alpha), ZERO));
+      }
+      // c = b'' + z
+      for (int r = 0; r < NS; ++r) {
+        FormDesc c = fcopy(w.cv + (size_t)r * s * nj, nj, R + (size_t)r * s * ld + S2 + s, ld, s, nj);
+        if (r == 0) { c.y = b1; c.ldy = nj; c.ay = ONE; }
+        if (r == NS - 1) { c.z = bn; c.ldz = nj; c.az = ONE; }
+        fc.push_back(c);
+      }
+      // x_i = Q^first_i c(2j) + Q^last_i c(2j+1) for block i of partition j
+      for (int j = 0; j < w.np; ++j)
+        for (int i = w.pa[j]; i <= w.pb[j]; ++i) {
+          z64* xi = w.x + (size_t)(i - 1) * s * nj;
+          gx1.push_back(gdesc(s, nj, s, plain(w.X[0] + (size_t)(i - 1) * ss2, s),
+                              plain(w.cv + (size_t)(2 * j) * s * nj, nj), xi, nj, ONE, ZERO));
+          gx2.push_back(gdesc(s, nj, s, plain(w.X[1] + (size_t)(i - 1) * ss2, s),
+                              plain(w.cv + (size_t)(2 * j + 1) * s * nj, nj), xi, nj, ONE, ONE));
+        }
     }
     LuDesc L{};
-    L.w = R; L.ldw = ld; L.s = 2 * s; L.ncols = ld; L.ipiv = w.ipr; L.info = info + p;
+    L.w = R; L.ldw = ld; L.s = S2; L.ncols = ld; L.ipiv = w.ipr; L.info = info + p;
     lu.push_back(L);
-    // G_1n of the open system = G11 w_top + G1n w_bot, w = R^-1 [0; 1]
-    gG1.push_back(gdesc(s, s, s, plain(G11, s), plain(R + 2 * s, ld), w.G1n, s, ONE, ZERO));
-    gG2.push_back(gdesc(s, s, s, plain(G1n, s), plain(R + (size_t)s * ld + 2 * s, ld), w.G1n, s, ONE, ONE));
+    // G_1n = g(slot 0, .) R^-1 E_last = G_aa w_0 + G_ab w_1 (w: the E_last solution in partition 0's slots)
+    gG1.push_back(gdesc(s, s, s, plain(w.Gc[0][0], s), plain(R + S2, ld), w.G1n, s, ONE, ZERO));
+    gG2.push_back(gdesc(s, s, s, plain(w.Gc[0][2], s), plain(R + (size_t)s * ld + S2, ld), w.G1n, s, ONE, ONE));
     // Gamma = i Sigma - i Sigma^H
     for (int q2 = 0; q2 < 2; ++q2) {
       FormDesc gm = fdesc(w.Gam[q2], s, s, s);
@@ -540,8 +867,8 @@ void build_boundary(ss_handle* h, std::vector<PW>& pts, int ninj, int* info, z64
   }
   B.form(f0);
   big_gemm(h, B, gR);
-  big_gemm(h, B, gb1);
-  big_gemm(h, B, gb2);
+  big_gemm(h, B, gbA);
+  big_gemm(h, B, gbB);
   big_gemm(h, B, gsb);
   ::lu(h, B, lu);
   big_gemm(h, B, gG1);
@@ -638,82 +965,197 @@ void build_ir_norms(Plan& N, std::vector<PW>& pts, int ninj, double* mm, double*
 }
 
 // Correction delta = M~^-1 r with the stored D_i^-1 (block UL substitution of
-// the first-column sweep) and R^-1 (Sherman-Morrison-Woodbury), then x += delta.
+// the first-column sweep, inside each partition) and R^-1 (Sherman-Morrison-
+// Woodbury with the merged boundary system), then x += delta:
+//   y = blockdiag(A_j)^-1 r (UL substitution per partition),
+//   delta = y - Q R^-1 K' B^T y.
 // FP64-accurate products (the exact tensor-core GEMM): with FP32 ones the
 // correction stops contracting on long devices (its error times the condition
 // number of A - Sigma nears 1).
-void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nmax) {
+void build_ir_correction(ss_handle* h, std::vector<PW>& pts, int ninj, int nsteps) {
   Plan& C = h->p_ir_cor;
   C.clear();
-  const int P = (int)pts.size();
-  // backward: w_n = Dn^-1 r_n ; w_i = Di^-1 (r_i - U_i w_{i+1})
-  for (int t = 0; t < nmax; ++t) {
+  // backward inside partition [a, b]: w_b = D_b^-1 r_b ; w_i = D_i^-1 (r_i - U_i w_{i+1})
+  for (int t = 0; t < nsteps; ++t) {
     std::vector<FormDesc> f;
     std::vector<GemmDesc> g1, g2;
     for (auto& w : pts) {
-      const int n = w.n, s = w.s;
-      if (t >= n) continue;
-      const int i = n - t;
+      const int s = w.s;
       const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
       const z64 E = make_double2(w.E, 0.0);
-      z64* ri = w.r + (i - 1) * bs;
-      z64* wi = w.wv + (i - 1) * bs;
-      if (i == n) {
-        g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(ri, ninj), wi, ninj, ONE, ZERO));
-      } else {
-        f.push_back(fcopy(w.tv, ninj, ri, ninj, s, ninj));
-        g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 1) * ss2, w.kd->Hu + (i - 1) * ss2, E, s),
-                           plain(wi + bs, ninj), w.tv, ninj, MONE, ONE));
-        g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, ONE, ZERO));
+      for (int j = 0; j < w.np; ++j) {
+        const int a = w.pa[j], b = w.pb[j];
+        if (t > b - a) continue;
+        const int i = b - t;
+        z64* ri = w.r + (i - 1) * bs;
+        z64* wi = w.wv + (i - 1) * bs;
+        z64* tj = w.tv + (size_t)j * bs;  // partition j's scratch
+        if (i == b) {
+          g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(ri, ninj), wi, ninj, ONE, ZERO));
+        } else {
+          f.push_back(fcopy(tj, ninj, ri, ninj, s, ninj));
+          g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 1) * ss2, w.kd->Hu + (i - 1) * ss2, E, s),
+                             plain(wi + bs, ninj), tj, ninj, MONE, ONE));
+          g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(tj, ninj), wi, ninj, ONE, ZERO));
+        }
       }
     }
     C.form(f);
     big_gemm(h, C, g1);
     big_gemm(h, C, g2);
   }
-  // forward: y_1 = w_1 ; y_i = w_i - Di^-1 (U_{i-1}^H y_{i-1})  (in place in w)
-  for (int t = 1; t < nmax; ++t) {
+  // forward inside the partition: y_a = w_a ; y_i = w_i - D_i^-1 (U_{i-1}^H y_{i-1})  (in place in w)
+  for (int t = 1; t < nsteps; ++t) {
     std::vector<GemmDesc> g1, g2;
     for (auto& w : pts) {
-      const int n = w.n, s = w.s;
-      if (t >= n) continue;
-      const int i = t + 1;
+      const int s = w.s;
       const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
       const z64 E = make_double2(w.E, 0.0);
-      z64* wi = w.wv + (i - 1) * bs;
-      g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 2) * ss2, w.kd->Hu + (i - 2) * ss2, E, s, 1),
-                         plain(wi - bs, ninj), w.tv, ninj, ONE, ZERO));
-      g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(w.tv, ninj), wi, ninj, MONE, ONE));
+      for (int j = 0; j < w.np; ++j) {
+        const int a = w.pa[j], b = w.pb[j];
+        if (t > b - a) continue;
+        const int i = a + t;
+        z64* wi = w.wv + (i - 1) * bs;
+        z64* tj = w.tv + (size_t)j * bs;
+        g1.push_back(gdesc(s, ninj, s, formed(w.kd->Su + (i - 2) * ss2, w.kd->Hu + (i - 2) * ss2, E, s, 1),
+                           plain(wi - bs, ninj), tj, ninj, ONE, ZERO));
+        g2.push_back(gdesc(s, ninj, s, plain(w.Dinv + (i - 1) * ss2, s), plain(tj, ninj), wi, ninj, MONE, ONE));
+      }
     }
     big_gemm(h, C, g1);
     big_gemm(h, C, g2);
   }
-  // SMW: z' = R^-1 [Sigma_L y_1 ; Sigma_R y_n] ; x_i += y_i + Q_i z'_top + P_i z'_bot
-  std::vector<GemmDesc> gz1, gz2, gr, gx1, gx2;
+  // SMW: zc = -K' B^T y ; z' = R^-1 zc ; x_i += y_i + Q^first_i z'(2j) + Q^last_i z'(2j+1)
+  std::vector<GemmDesc> gz, gr, gx1, gx2;
   std::vector<FormDesc> fx;
   for (auto& w : pts) {
-    const int n = w.n, s = w.s;
+    const int s = w.s, S2 = w.rows(), NS = 2 * w.np;
     const size_t ss2 = (size_t)s * s, bs = (size_t)s * ninj;
-    const int ld = 3 * s + ninj + 2 * s;
-    gz1.push_back(gdesc(s, ninj, s, plain(w.sig[0], s), plain(w.wv, ninj), w.zc, ninj, ONE, ZERO));
-    gz2.push_back(gdesc(s, ninj, s, plain(w.sig[1], s), plain(w.wv + (n - 1) * bs, ninj), w.zc + bs, ninj, ONE, ZERO));
-    gr.push_back(gdesc(2 * s, ninj, 2 * s, plain(w.Rw + 3 * s + ninj, ld), plain(w.zc, ninj), w.tv, ninj, ONE, ZERO));
-    for (int i = 0; i < n; ++i) {
-      z64* xi = w.x + i * bs;
-      FormDesc fd = fcopy(xi, ninj, xi, ninj, s, ninj);
-      fd.y = w.wv + i * bs; fd.ldy = ninj; fd.ay = ONE;
-      fx.push_back(fd);
-      gx1.push_back(gdesc(s, ninj, s, plain(w.X[0] + i * ss2, s), plain(w.tv, ninj), xi, ninj, ONE, ONE));
-      gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + i * ss2, s), plain(w.tv + bs, ninj), xi, ninj, ONE, ONE));
+    const int ld = bound_ld(w, ninj, true);
+    for (int r = 0; r < NS; ++r) {
+      const KTerm k = kterm(w, r);
+      const int blk = (k.t & 1) ? w.pb[k.t / 2] : w.pa[k.t / 2];
+      gz.push_back(gdesc(s, ninj, s, k.op, plain(w.wv + (size_t)(blk - 1) * bs, ninj), w.zc + (size_t)r * bs, ninj,
+                         zneg(k.alpha), ZERO));
     }
+    gr.push_back(gdesc(S2, ninj, S2, plain(w.Rw + S2 + s + ninj, ld), plain(w.zc, ninj), w.tv, ninj, ONE, ZERO));
+    for (int j = 0; j < w.np; ++j)
+      for (int i = w.pa[j]; i <= w.pb[j]; ++i) {
+        z64* xi = w.x + (size_t)(i - 1) * bs;
+        FormDesc fd = fcopy(xi, ninj, xi, ninj, s, ninj);
+        fd.y = w.wv + (size_t)(i - 1) * bs; fd.ldy = ninj; fd.ay = ONE;
+        fx.push_back(fd);
+        gx1.push_back(gdesc(s, ninj, s, plain(w.X[0] + (size_t)(i - 1) * ss2, s), plain(w.tv + (size_t)(2 * j) * bs, ninj),
+                            xi, ninj, ONE, ONE));
+        gx2.push_back(gdesc(s, ninj, s, plain(w.X[1] + (size_t)(i - 1) * ss2, s),
+                            plain(w.tv + (size_t)(2 * j + 1) * bs, ninj), xi, ninj, ONE, ONE));
+      }
   }
-  big_gemm(h, C, gz1);
-  big_gemm(h, C, gz2);
+  big_gemm(h, C, gz);
   big_gemm(h, C, gr);
   C.form(fx);
   big_gemm(h, C, gx1);
   big_gemm(h, C, gx2);
-  (void)P;
+}
+
+// ----------------------------------------------------- density of states
+// rho_i = -Im Tr[G_ii] / pi for every block of the open system G = (A - Sigma)^-1
+// (Eq. negf; the spectral weight the observables of Sec. 2B are built from).
+// Two sweeps over M = A - Sigma_L (+) Sigma_R, run together: the backward one
+// keeps the right-connected Schur products SR_i = A_{i,i+1} X_{i+1}
+// (X_{i+1} = D_{i+1}^-1 A_{i+1,i}), the forward one the left-connected
+// SL_i = A_{i,i-1} Y_{i-1}, each in one block column store.  Then
+// G_ii = (M_ii - SL_i - SR_i)^-1 for all blocks (batched LUs with identity
+// right-hand sides, DOS_ROUND blocks per point at a time) and the trace of
+// its diagonal.  The sweeps' last blocks need no factorisation.
+void build_dos_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nmax) {
+  Plan& S = h->p_sweep;
+  S.clear();
+  const int P = (int)pts.size();
+  S.memset0(info, sizeof(int) * 2 * (size_t)P * nmax);
+  for (int t = 0; t < nmax; ++t) {
+    std::vector<GemmDesc> g;
+    std::vector<FormDesc> f, fc;
+    std::vector<LuDesc> lu;
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const int n = w.n, s = w.s;
+      if (t >= n) continue;
+      const KData* kd = w.kd;
+      const size_t ss2 = (size_t)s * s;
+      const z64 E = make_double2(w.E, 0.0);
+      for (int dir = 0; dir < 2; ++dir) {
+        const int i = dir == 0 ? n - t : t + 1;
+        z64* store = w.X[dir] + (size_t)(i - 1) * ss2;  // SR_i (dir 0) / SL_i (dir 1)
+        if (t > 0) {
+          const int up = dir == 0 ? i - 1 : i - 2;
+          g.push_back(gdesc(s, s, s, formed(kd->Su + up * ss2, kd->Hu + up * ss2, E, s, dir == 0 ? 0 : 1),
+                            plain(w.Xl[0][dir][(t - 1) & 1], s), store, s, ONE, ZERO));
+        }
+        if (t == n - 1) continue;  // the block the sweep ends on: nothing further needs D_i
+        z64* W = w.Ws[0][dir];
+        const int ld = 2 * s;
+        // D_i = M_ii - (Schur product): the lead term enters at the sweep's first block
+        FormDesc d = fformed(W, ld, kd->Sd + (i - 1) * ss2, kd->Hd + (i - 1) * ss2, E, s, s, s);
+        if (t > 0) { d.z = store; d.ldz = s; d.az = MONE; }
+        if (t == 0) { d.v = w.sig[dir == 0 ? 1 : 0]; d.ldv = s; d.av = MONE; }
+        f.push_back(d);
+        if (dir == 0) f.push_back(fformed(W + s, ld, kd->Su + (i - 2) * ss2, kd->Hu + (i - 2) * ss2, E, s, s, s, 1));
+        else f.push_back(fformed(W + s, ld, kd->Su + (i - 1) * ss2, kd->Hu + (i - 1) * ss2, E, s, s, s, 0));
+        LuDesc L{};
+        L.w = W; L.ldw = ld; L.s = s; L.ncols = 2 * s; L.ipiv = w.ips[0][dir];
+        L.info = info + (size_t)(2 * p + dir) * nmax + t;
+        lu.push_back(L);
+        fc.push_back(fcopy(w.Xl[0][dir][t & 1], s, W + s, ld, s, s));
+      }
+    }
+    big_gemm(h, S, g);
+    S.form(f);
+    ::lu(h, S, lu);
+    S.form(fc);
+  }
+}
+
+// Diagonal blocks, DOS_ROUND per point per round: [M_ii - SL_i - SR_i | 1] -> LU
+// -> G_ii in the right-hand side -> Tr into traces[p * nmax + i - 1].
+void build_dos_diag(ss_handle* h, std::vector<PW>& pts, int* info, z64* traces, int nmax) {
+  Plan& B = h->p_bound;
+  B.clear();
+  const int P = (int)pts.size();
+  B.memset0(info, sizeof(int) * (size_t)P * nmax);
+  for (int r0 = 0; r0 < nmax; r0 += DOS_ROUND) {
+    std::vector<FormDesc> f;
+    std::vector<LuDesc> lu;
+    std::vector<TraceDesc> tr;
+    for (int p = 0; p < P; ++p) {
+      PW& w = pts[p];
+      const int n = w.n, s = w.s;
+      const KData* kd = w.kd;
+      const size_t ss2 = (size_t)s * s;
+      const z64 E = make_double2(w.E, 0.0);
+      for (int q = 0; q < DOS_ROUND; ++q) {
+        const int i = r0 + q + 1;
+        if (i > n) break;
+        z64* K = w.Kw + (size_t)q * 2 * ss2;
+        FormDesc d = fformed(K, 2 * s, kd->Sd + (i - 1) * ss2, kd->Hd + (i - 1) * ss2, E, s, s, s);
+        // two of: SR_i (i < n), SL_i (i > 1), Sigma_L (i = 1), Sigma_R (i = n)
+        const z64* t1 = i < n ? w.X[0] + (size_t)(i - 1) * ss2 : w.sig[1];
+        const z64* t2 = i > 1 ? w.X[1] + (size_t)(i - 1) * ss2 : w.sig[0];
+        d.z = t1; d.ldz = s; d.az = MONE;
+        d.v = t2; d.ldv = s; d.av = MONE;
+        f.push_back(d);
+        f.push_back(fident(K + s, 2 * s, s, s, 1.0));
+        LuDesc L{};
+        L.w = K; L.ldw = 2 * s; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipk + (size_t)q * s;
+        L.info = info + (size_t)p * nmax + i - 1;
+        lu.push_back(L);
+        tr.push_back({K + s, 2 * s, nullptr, 0, s, traces + (size_t)p * nmax + i - 1, nullptr});
+      }
+    }
+    B.form(f);
+    ::lu(h, B, lu);
+    B.trace(tr);
+  }
 }
 
 bool same_points(const ss_handle* h, int n, const double* E, const int* k) {
@@ -746,11 +1188,14 @@ int ensure_scalars(ss_handle* h, size_t ni, size_t nd, size_t nt) {
 struct Want {
   bool sigma_out = false;
   bool solve = false;   // sweeps + boundary + trace
+  bool dos = false;     // density of states per block (instead of solve)
   int ninj = 0;
   const ss_c64* inj = nullptr;
   ss_c64* x = nullptr;
   ss_c64* sigL = nullptr;
   ss_c64* sigR = nullptr;
+  double* dos_out = nullptr;
+  Layout layout() const { return dos ? LAYOUT_DOS : (solve && !x ? LAYOUT_LEAN : LAYOUT_FULL); }
 };
 
 int worst(int a, int b) { return a != SS_OK ? a : b; }
@@ -769,8 +1214,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
   T.assign(n_pts, 0.0);
   Ti.assign(n_pts, 0.0);
   // offsets of per-point packed arrays
-  std::vector<size_t> off_ss(n_pts), off_inj(n_pts), off_x(n_pts);
-  size_t a_ss = 0, a_inj = 0, a_x = 0;
+  std::vector<size_t> off_ss(n_pts), off_inj(n_pts), off_x(n_pts), off_n(n_pts);
+  size_t a_ss = 0, a_inj = 0, a_x = 0, a_n = 0;
   std::vector<int> order(n_pts);
   for (int i = 0; i < n_pts; ++i) {
     auto it = h->ks.find(k_id[i]);
@@ -780,6 +1225,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     off_ss[i] = a_ss; a_ss += (size_t)s * s;
     off_inj[i] = a_inj; a_inj += (size_t)2 * s * want.ninj;
     off_x[i] = a_x; a_x += (size_t)n * s * want.ninj;
+    off_n[i] = a_n; a_n += (size_t)n;
     order[i] = i;
   }
   // longest-processing-time first
@@ -788,11 +1234,26 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     const KData& kb = h->ks[k_id[b]];
     return (double)ka.n * ka.s * ka.s * ka.s > (double)kb.n * kb.s * kb.s * kb.s;
   });
-  // reuse of the previous call's self-energies when the point list is identical
-  const bool reuse_sigma = h->c_sigma && same_points(h, n_pts, E, k_id) && n_pts <= h->cfg.max_points;
   const bool dp = h->cfg.device_ptrs != 0;
   cudaStream_t st = h->stream;
   int rc_all = SS_OK;
+  const Layout layout = want.layout();
+  const int parts = layout == LAYOUT_DOS ? 1 : h->cfg.partitions;
+  // reuse of the previous call's self-energies when the point list is
+  // identical and, in this call's layout too, forms one batch (the doubling
+  // buffers then sit at the same addresses)
+  bool one_batch = n_pts <= h->cfg.max_points;
+  {
+    size_t tot = 0;
+    for (int i = 0; i < n_pts && one_batch; ++i) {
+      const KData& kd = h->ks[k_id[i]];
+      tot += point_bytes(kd.n, kd.s, h->cfg.max_inj, h->mixed(), layout, parts);
+    }
+    one_batch = one_batch && tot <= h->arena_bytes;
+  }
+  const bool reuse_sigma = h->c_sigma && same_points(h, n_pts, E, k_id) && one_batch;
+  // the first-column sweep keeps D_i^-1 only when x is refined
+  const bool refine = h->mixed() && layout == LAYOUT_FULL && want.x && want.ninj > 0;
 
   size_t pos = 0;
   while (pos < (size_t)n_pts) {
@@ -802,12 +1263,13 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     while (pos < (size_t)n_pts && (int)pts.size() < h->cfg.max_points) {
       const int i = order[pos];
       const KData& kd = h->ks[k_id[i]];
-      const size_t need = point_bytes(kd.n, kd.s, h->cfg.max_inj, h->mixed());
+      const size_t need = point_bytes(kd.n, kd.s, h->cfg.max_inj, h->mixed(), layout, parts);
       if (!pts.empty() && bytes + need > h->arena_bytes) break;
       if (need > h->arena_bytes) return fail(h, SS_ERR_OOM, "one point does not fit the workspace");
       bytes += need;
       PW w;
-      w.idx = i; w.n = kd.n; w.s = kd.s; w.E = E[i]; w.kd = &kd;
+      w.idx = i; w.n = kd.n; w.s = kd.s; w.E = E[i]; w.kd = &kd; w.layout = layout;
+      set_partitions(w, parts);
       pts.push_back(w);
       ++pos;
     }
@@ -815,18 +1277,22 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     // the layout depends only on (n, s) and max_inj, so cached self-energies
     // stay at the same addresses whatever n_inj the next call uses
     Carve c(h->arena);
+    carve_batch(c, pts, h->cfg.max_inj, h->mixed());
     int nmax = 0;
-    for (auto& w : pts) { carve_point(c, w, h->cfg.max_inj, h->mixed()); nmax = std::max(nmax, w.n); }
-    // device scalars: act, iters, conv (2P each), decim info (4P), sweep info (2P*nmax), bound info (P)
-    const size_t ni = 2 * P * 3 + 4 * P + 2 * (size_t)P * nmax + P;
-    int rc = ensure_scalars(h, ni, 3 * 2 * P + 4 * P, P);
+    for (auto& w : pts) nmax = std::max(nmax, w.n);
+    const int nsteps = sweep_steps(pts);
+    // device scalars: act, iters, conv (2P each), decim info (4P), sweep info
+    // (2 MAXP P nsteps), boundary / density-of-states info (P nmax)
+    const size_t n_sinfo = 2 * (size_t)MAXP * P * std::max(nsteps, 1);
+    const size_t ni = 2 * P * 3 + 4 * P + n_sinfo + (size_t)P * nmax;
+    int rc = ensure_scalars(h, ni, 3 * 2 * P + 4 * P + (size_t)P * nmax, (size_t)P * nmax);
     if (rc) return rc;
     int* act = h->dint;
     int* itr = act + 2 * P;
     int* conv = itr + 2 * P;
     int* dinfo = conv + 2 * P;
     int* sinfo = dinfo + 4 * P;
-    int* binfo = sinfo + 2 * (size_t)P * nmax;
+    int* binfo = sinfo + n_sinfo;
     double* na = h->ddbl;
     double* nb = na + 2 * P;
     double* nd = nb + 2 * P;
@@ -834,9 +1300,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     double* bb = rr + P;
     double* mm = bb + P;
     double* xx = mm + P;
+    double* dosv = xx + P;    // density of states, P x nmax
 
     // inputs
-    if (want.solve && want.ninj > 0) {
+    if (want.solve && want.ninj > 0 && layout == LAYOUT_FULL) {
       for (auto& w : pts) {
         const size_t cnt = (size_t)2 * w.s * want.ninj;
         const ss_c64* src = want.inj + off_inj[w.idx];
@@ -848,10 +1315,38 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
 
     // 1. self-energies
     std::vector<int> h_it(2 * P, 0), h_conv(2 * P, 1), h_dinfo(4 * P, 0);
+    std::vector<int> seeded;  // 2 per point: lead seeded by an accepted warm start
     if (!reuse_sigma) {
       h->plan_error = false;
-      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd);
+      if (h->cfg.warm_start) {
+        // learned warm start of each lead that has a network attached (points
+        // of the network's block size); rejected seeds fall back to the doubling
+        seeded.assign(2 * P, 0);
+        for (int side = 0; side < 2; ++side) {
+          if (!h->warm_net[side]) continue;
+          int n_in = 0, n_out = 0, mb = 0;
+          mlp_dims(h->warm_net[side], &n_in, &n_out, &mb);
+          std::vector<PW> sub;
+          std::vector<int> where;
+          std::vector<double> kv;
+          for (int p = 0; p < P; ++p)
+            if (2 * pts[p].s * pts[p].s == n_out) { sub.push_back(pts[p]); where.push_back(p); kv.push_back(pts[p].kd->kval); }
+          if (sub.empty()) continue;
+          std::vector<int> acc;
+          const int r = warm_seed(h, sub, side, kv, WARM_ITERS, WARM_TOL, dinfo, acc);
+          if (r) return r;
+          for (size_t q = 0; q < sub.size(); ++q) seeded[2 * where[q] + side] = acc[q];
+        }
+      }
+      const bool preset = !seeded.empty();
+      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd, preset, preset ? &seeded : nullptr);
       if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the doubling");
+      if (preset) {
+        std::vector<int> init(2 * P);
+        for (int i = 0; i < 2 * P; ++i) init[i] = seeded[i] ? 0 : 1;
+        CK(cudaMemcpyAsync(act, init.data(), sizeof(int) * 2 * P, cudaMemcpyHostToDevice, st), "flags");
+        CK(cudaStreamSynchronize(st), "flags");
+      }
       CK(h->p_setup.upload(st), "upload setup");
       CK(h->p_iter[0].upload(st), "upload iter");
       CK(h->p_iter[1].upload(st), "upload iter");
@@ -896,6 +1391,9 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       CK(cudaMemcpyAsync(h_it.data(), itr, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read iters");
       CK(cudaMemcpyAsync(h_conv.data(), conv, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read conv");
       CK(cudaMemcpyAsync(h_dinfo.data(), dinfo, sizeof(int) * 4 * P, cudaMemcpyDeviceToHost, st), "read info");
+      CK(cudaStreamSynchronize(st), "self-energy sync");
+      for (int i = 0; i < (int)seeded.size(); ++i)
+        if (seeded[i]) { h_conv[i] = 1; h_it[i] = -WARM_ITERS; }  // accepted seed: converged, steps as negative count
     } else {
       for (int p = 0; p < P; ++p) {
         h_it[2 * p] = h->c_iters[2 * pts[p].idx];
@@ -911,25 +1409,46 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       }
     }
 
-    // 2.-4. sweeps, boundary, transmission
-    std::vector<int> h_sinfo, h_binfo(P, 0);
+    // 2.-4. sweeps, boundary, transmission (or the density of states)
+    std::vector<int> h_sinfo, h_binfo;
     std::vector<z64> h_tr(P);
     std::vector<double> ir_err(P, -1.0);
-    int ir_steps = 0;
+    if (want.dos) {
+      h->plan_error = false;
+      build_dos_sweeps(h, pts, sinfo, nmax);
+      build_dos_diag(h, pts, binfo, h->dtr, nmax);
+      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the sweeps");
+      CK(h->p_sweep.upload(st), "upload sweeps");
+      CK(h->p_bound.upload(st), "upload diagonal blocks");
+      CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
+      CK(h->p_bound.run(st, &h->nlaunch, h->P()), "diagonal blocks");
+      launch_scaled_imag(h->dtr, dosv, P * nmax, -1.0 / M_PI, st);
+      ++h->nlaunch;
+      CK(cudaGetLastError(), "density of states");
+      for (int p = 0; p < P; ++p) {
+        const PW& w = pts[p];
+        CK(cudaMemcpyAsync(want.dos_out + off_n[w.idx], dosv + (size_t)p * nmax, sizeof(double) * w.n,
+                           dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st), "copy dos");
+      }
+      h_sinfo.assign(2 * (size_t)P * nmax, 0);
+      h_binfo.assign((size_t)P * nmax, 0);
+      CK(cudaMemcpyAsync(h_sinfo.data(), sinfo, sizeof(int) * h_sinfo.size(), cudaMemcpyDeviceToHost, st), "info");
+      CK(cudaMemcpyAsync(h_binfo.data(), binfo, sizeof(int) * h_binfo.size(), cudaMemcpyDeviceToHost, st), "info");
+    }
     if (want.solve) {
       h->plan_error = false;
-      build_sweeps(h, pts, sinfo, nmax);
-      build_boundary(h, pts, want.x ? want.ninj : 0, binfo, h->dtr);
+      build_sweeps(h, pts, sinfo, nsteps, refine);
+      build_boundary(h, pts, want.x ? want.ninj : 0, binfo, h->dtr, refine);
       if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the sweeps");
       CK(h->p_sweep.upload(st), "upload sweeps");
       CK(h->p_bound.upload(st), "upload boundary");
       CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
       CK(h->p_bound.run(st, &h->nlaunch, h->P()), "boundary");
-      if (h->mixed() && want.x && want.ninj > 0) {
+      if (refine) {
         // FP64 iterative refinement of x until the normwise backward error
         // ||r|| / (||A - Sigma|| ||x|| + ||Inj||) (Frobenius norms) is <= ir_tol
         build_ir_residual(h, pts, want.ninj, rr, xx);
-        build_ir_correction(h, pts, want.ninj, nmax);
+        build_ir_correction(h, pts, want.ninj, nsteps);
         if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the refinement");
         Plan nrm;
         build_ir_norms(nrm, pts, want.ninj, mm, bb);
@@ -953,7 +1472,6 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
             ir_err[p] = rel;
             worst_rel = std::max(worst_rel, std::isfinite(rel) ? rel : 1e300);
           }
-          ir_steps = it;
           // stop at the tolerance, at the cap, or when a correction no longer
           // halves the residual (FP64 working accuracy: more steps cannot help)
           if (worst_rel <= h->cfg.ir_tol || it >= h->cfg.ir_max_iter || worst_rel > 0.5 * prev) break;
@@ -961,7 +1479,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
           CK(h->p_ir_cor.run(st, &h->nlaunch, h->P()), "correction");
         }
       }
-      h_sinfo.assign(2 * (size_t)P * nmax, 0);
+      h_sinfo.assign(n_sinfo, 0);
+      h_binfo.assign(P, 0);
       CK(cudaMemcpyAsync(h_sinfo.data(), sinfo, sizeof(int) * h_sinfo.size(), cudaMemcpyDeviceToHost, st), "info");
       CK(cudaMemcpyAsync(h_binfo.data(), binfo, sizeof(int) * P, cudaMemcpyDeviceToHost, st), "info");
       CK(cudaMemcpyAsync(h_tr.data(), h->dtr, sizeof(z64) * P, cudaMemcpyDeviceToHost, st), "read T");
@@ -977,7 +1496,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     if (h->cfg.profile) h->prof.collect();
 
     for (int p = 0; p < P; ++p) {
-      const int i = pts[p].idx;
+      const PW& w = pts[p];
+      const int i = w.idx;
       iters[2 * i] = h_it[2 * p];
       iters[2 * i + 1] = h_it[2 * p + 1];
       int stt = SS_OK;
@@ -986,15 +1506,26 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
         for (int q = 0; q < 4; ++q)
           if (h_dinfo[(q < 2 ? 2 * p + q : 2 * P + 2 * p + q - 2)] && stt == SS_OK) stt = SS_ERR_SINGULAR;
       }
+      if (want.dos) {
+        bool bad = false;
+        for (int d = 0; d < 2; ++d)
+          for (int t = 0; t < nmax; ++t) bad = bad || h_sinfo[(size_t)(2 * p + d) * nmax + t] != 0;
+        for (int t = 0; t < w.n; ++t) bad = bad || h_binfo[(size_t)p * nmax + t] != 0;
+        if (bad && stt == SS_OK) {
+          stt = SS_ERR_SINGULAR;
+          if (h->err.empty()) h->err = "singular block in the density of states of point " + std::to_string(i);
+        }
+      }
       if (want.solve) {
-        for (int d = 0; d < 2 && stt == SS_OK; ++d)
-          for (int t = 0; t < nmax; ++t)
-            if (h_sinfo[(size_t)(2 * p + d) * nmax + t]) {
-              stt = SS_ERR_SINGULAR;
-              if (h->err.empty())
-                h->err = "singular diagonal block in the sweep of point " + std::to_string(i);
-              break;
-            }
+        for (int j = 0; j < w.np && stt == SS_OK; ++j)
+          for (int d = 0; d < 2 && stt == SS_OK; ++d)
+            for (int t = 0; t < nsteps; ++t)
+              if (h_sinfo[sinfo_index(p, j, d, t, nsteps)]) {
+                stt = SS_ERR_SINGULAR;
+                if (h->err.empty())
+                  h->err = "singular diagonal block in the sweep of point " + std::to_string(i);
+                break;
+              }
         if (h_binfo[p] && stt == SS_OK) stt = SS_ERR_SINGULAR;
         if (ir_err[p] >= 0.0) {
           err_out[i] = ir_err[p];
@@ -1014,7 +1545,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
   // cache
   h->cE.assign(E, E + n_pts);
   h->cK.assign(k_id, k_id + n_pts);
-  h->c_sigma = n_pts <= h->cfg.max_points;
+  h->c_sigma = one_batch;
   h->c_iters = iters;
   h->c_T = want.solve && n_pts <= h->cfg.max_points;
   h->cT = T;
@@ -1073,6 +1604,8 @@ void ss_config_default(ss_config* cfg) {
   cfg->device_ptrs = 0;
   cfg->use_graphs = 1;
   cfg->profile = 0;
+  cfg->partitions = 1;
+  cfg->memory_lean = 0;
 }
 
 int ss_create(ss_handle** hp, const ss_config* cfg) {
@@ -1094,6 +1627,10 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     g_create_error = "invalid eta / decim_tol / decim_max_iter";
     return SS_ERR_ARG;
   }
+  if (cfg->partitions < 1 || cfg->partitions > MAXP) {
+    g_create_error = "partitions outside 1.." + std::to_string(MAXP);
+    return SS_ERR_ARG;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev < 1) {
@@ -1111,7 +1648,8 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     h->own_stream = true;
   }
   h->arena_bytes = (size_t)cfg->max_points *
-                   point_bytes(cfg->n_b_max, cfg->s_b_max, cfg->max_inj, cfg->precision == SS_MIXED_OZAKI);
+                   point_bytes(cfg->n_b_max, cfg->s_b_max, cfg->max_inj, cfg->precision == SS_MIXED_OZAKI,
+                               cfg->memory_lean ? LAYOUT_LEAN : LAYOUT_FULL, cfg->partitions);
   e = cudaMalloc(&h->arena, h->arena_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1131,6 +1669,17 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
     const size_t ex = (((size_t)s * sizeof(int)) + 1023) & ~size_t(1023);
     const size_t per_lead = 2 * (a1 + ex) + 2 * (b1 + ex);
     h->pack_bytes = (size_t)cfg->max_points * 2 * per_lead + (4 << 20);
+    // the partition merge's largest single product: R^-1 (2 np s square) times
+    // the refinement's SMW right-hand side
+    const int np = std::min(cfg->partitions, cfg->n_b_max);
+    if (np > 1) {
+      const int S2 = 2 * np * s;
+      GemmDesc g{};
+      g.m = S2; g.n = std::max(cfg->max_inj, 1); g.k = S2;
+      static const z64 da = {0.0, 0.0}, db = {0.0, 0.0};
+      g.a.p = &da; g.b.p = &db;
+      h->pack_bytes = std::max(h->pack_bytes, Plan::oz_pack_bytes(std::vector<GemmDesc>(1, g)) + (4 << 20));
+    }
     e = cudaMalloc(&h->pack, h->pack_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->tc_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->tc_err, 0, sizeof(int));
@@ -1278,6 +1827,21 @@ int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, d
   return rc;
 }
 
+int ss_dos(ss_handle* h, int n_pts, const double* E, const int* k_id, double* dos, int* status) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  if (!dos && n_pts > 0) return fail(h, SS_ERR_ARG, "NULL dos");
+  Want w;
+  w.dos = true;
+  w.dos_out = dos;
+  std::vector<int> st, it;
+  std::vector<double> T, Ti;
+  int rc = run_points(h, n_pts, E, k_id, w, st, it, T, Ti);
+  if (status) for (size_t i = 0; i < st.size(); ++i) status[i] = st[i];
+  h->c_T = false;
+  return rc;
+}
+
 int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb_out, int* nbo_out,
                 int* upd_out, double* ms_out) {
   if (!h) return SS_ERR_ARG;
@@ -1388,11 +1952,23 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   return report(best);
 }
 
+int ss_set_momentum(ss_handle* h, int k_id, double k) {
+  if (!h) return SS_ERR_ARG;
+  h->err.clear();
+  auto it = h->ks.find(k_id);
+  if (it == h->ks.end()) return fail(h, SS_ERR_STATE, "no Hamiltonian set for k_id " + std::to_string(k_id));
+  if (!std::isfinite(k)) return fail(h, SS_ERR_ARG, "non-finite momentum");
+  it->second.kval = k;
+  h->c_sigma = h->c_T = false;
+  return SS_OK;
+}
+
 int ss_set_warm_start(ss_handle* h, ss_mlp* net, int side, double out_scale) {
   if (!h) return SS_ERR_ARG;
   if (side < 0 || side > 1 || !(out_scale > 0.0)) return fail(h, SS_ERR_ARG, "side must be 0/1, out_scale > 0");
   h->warm_net[side] = net;
   h->warm_scale[side] = out_scale;
+  h->c_sigma = h->c_T = false;
   return SS_OK;
 }
 
@@ -1423,7 +1999,7 @@ int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, con
       if (it == h->ks.end()) return fail(h, SS_ERR_STATE, "no Hamiltonian for k_id " + std::to_string(k_id[base + p]));
       PW& w = pts[p];
       w.idx = base + p; w.n = it->second.n; w.s = it->second.s; w.E = E[base + p]; w.kd = &it->second;
-      carve_point(c, w, h->cfg.max_inj, h->mixed());
+      carve_doubling(c, w);  // only the doubling buffers are used
       smax = std::max(smax, w.s);
     }
     if (c.off > h->arena_bytes) return fail(h, SS_ERR_OOM, "workspace too small for the chunk");
@@ -1438,118 +2014,13 @@ int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, con
     double* nb = na + NP;
     double* nd = nb + NP;
     std::vector<int> accepted(P, 0);
-    const double eta = h->cfg.eta;
     // ---------------- warm start: network seed, fixed-point steps, residual judge
     if (net) {
-      const int s = pts[0].s;
-      for (auto& w : pts)
-        if (w.s != s || 2 * s * s != n_out) return fail(h, SS_ERR_ARG, "network output does not match s_b");
-      if (P > mb) return fail(h, SS_ERR_ARG, "network max_batch below max_points");
-      const size_t need = (size_t)P_max * (n_in + n_out);
-      if (need > h->warm_cap) {
-        cudaFree(h->feat); cudaFree(h->warm_y); cudaFree(h->wres);
-        h->feat = nullptr; h->warm_y = nullptr; h->wres = nullptr;
-        CK(cudaMalloc(&h->feat, (size_t)P_max * n_in * sizeof(float)), "warm features");
-        CK(cudaMalloc(&h->warm_y, (size_t)P_max * n_out * sizeof(float)), "warm outputs");
-        CK(cudaMalloc(&h->wres, (size_t)P_max * sizeof(double)), "warm residuals");
-        h->warm_cap = need;
-      }
-      std::vector<float> f((size_t)P * n_in, 0.f);
-      for (int p = 0; p < P; ++p) {
-        const double e = E[base + p], k = kval[base + p];
-        float* r = &f[(size_t)p * n_in];
-        r[0] = (float)e; r[1] = (float)std::cos(k); r[2] = (float)std::sin(k);
-        for (int m = 1; m <= 8 && 3 + 2 * m - 1 < n_in; ++m) {
-          r[3 + 2 * (m - 1)] = (float)std::sin(m * M_PI * e);
-          r[4 + 2 * (m - 1)] = (float)std::cos(m * M_PI * e);
-        }
-      }
-      cudaStream_t ns = mlp_stream(net);
-      CK(cudaMemcpyAsync(h->feat, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, ns), "features");
-      int r2 = ss_mlp_forward(net, P, h->feat, h->warm_y);
-      if (r2 != SS_OK) return fail(h, r2, "network forward failed");
-      cudaEvent_t ev;
-      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
-      cudaEventRecord(ev, ns);
-      cudaStreamWaitEvent(st, ev, 0);
-      cudaEventDestroy(ev);
-      for (int p = 0; p < P; ++p)
-        launch_unpack_g(h->warm_y + (size_t)p * n_out, s, 1.0 / h->warm_scale[side], pts[p].es[side], s, st);
-      // lead blocks at z and one fixed-point step g <- (D - U g L)^-1 (right) / (D - L g U)^-1 (left)
-      Plan& setup = h->p_setup;
-      setup.clear();
-      std::vector<FormDesc> fl;
-      for (auto& w : pts) {
-        const z64 z = make_double2(w.E, eta);
-        const z64* const* cc = w.kd->cell[side];
-        fl.push_back(fformed(w.D[side], s, cc[2], cc[0], z, s, s, s));
-        fl.push_back(fformed(w.a[side][0], s, cc[3], cc[1], z, s, s, s));
-        fl.push_back(fformed(w.b[side][0], s, cc[3], cc[1], z, s, s, s, 1));
-      }
-      setup.form(fl);
-      Plan& I = h->p_warm_iter;
-      I.clear();
-      std::vector<GemmDesc> g1, g2;
-      std::vector<FormDesc> f1, f2;
-      std::vector<LuDesc> lus;
-      for (int p = 0; p < P; ++p) {
-        PW& w = pts[p];
-        const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
-        const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
-        z64* W = w.Wd[side];
-        g1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
-        f1.push_back(fcopy(W, 2 * s, w.D[side], s, s, s));
-        f1.push_back(fident(W + s, 2 * s, s, s, 1.0));
-        g2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, 2 * s, MONE, ONE));
-        LuDesc L{};
-        L.w = W; L.ldw = 2 * s; L.s = s; L.ncols = 2 * s; L.ipiv = w.ipd[side]; L.info = dinfo + 2 * p + side;
-        lus.push_back(L);
-        f2.push_back(fcopy(w.es[side], s, W + s, 2 * s, s, s));
-      }
-      I.memset0(dinfo, sizeof(int) * 4 * P);
-      big_gemm(h, I, g1);
-      I.form(f1);
-      big_gemm(h, I, g2);
-      ::lu(h, I, lus);
-      I.form(f2);
-      // judge: ||g (D - U g L) - 1||_F^2 into wres
-      Plan& J = h->p_warm_judge;
-      J.clear();
-      std::vector<GemmDesc> j1, j2, j3;
-      std::vector<FormDesc> jf;
-      std::vector<Norm1Desc> fr;
-      J.memset0(h->wres, sizeof(double) * P);
-      for (int p = 0; p < P; ++p) {
-        PW& w = pts[p];
-        const z64* first = side == 1 ? w.a[side][0] : w.b[side][0];
-        const z64* second = side == 1 ? w.b[side][0] : w.a[side][0];
-        z64* W = w.Wd[side];
-        j1.push_back(gdesc(s, s, s, plain(first, s), plain(w.es[side], s), w.T1[side], s, ONE, ZERO));
-        jf.push_back(fcopy(W, s, w.D[side], s, s, s));
-        j2.push_back(gdesc(s, s, s, plain(w.T1[side], s), plain(second, s), W, s, MONE, ONE));
-        GemmDesc q = gdesc(s, s, s, plain(w.es[side], s), plain(W, s), w.T2[side], s, ONE, MONE);
-        q.cmode = 2;
-        j3.push_back(q);
-        fr.push_back({w.T2[side], s, s, s, h->wres + p, nullptr});
-      }
-      // the judge runs in FP64 whatever the precision mode
-      J.gemm(j1);
-      J.form(jf);
-      J.gemm(j2);
-      J.gemm(j3);
-      J.frob2(fr);
-      if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small");
-      CK(setup.upload(st), "upload warm");
-      CK(I.upload(st), "upload warm");
-      CK(J.upload(st), "upload warm");
-      CK(setup.run(st, &h->nlaunch, h->P()), "warm setup");
-      for (int it = 0; it < warm_iters; ++it) CK(I.run(st, &h->nlaunch, h->P()), "warm step");
-      CK(J.run(st, &h->nlaunch, h->P()), "warm judge");
-      std::vector<double> res(P);
-      CK(cudaMemcpyAsync(res.data(), h->wres, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read residual");
-      CK(cudaStreamSynchronize(st), "warm sync");
-      for (int p = 0; p < P; ++p)
-        accepted[p] = std::isfinite(res[p]) && std::sqrt(res[p] / (double)s) <= warm_tol ? 1 : 0;
+      std::vector<double> kv(P);
+      for (int p = 0; p < P; ++p) kv[p] = kval[base + p];
+      h->plan_error = false;
+      rc = warm_seed(h, pts, side, kv, warm_iters, warm_tol, dinfo, accepted);
+      if (rc) return rc;
     }
     // ---------------- plain doubling for the others (this lead only)
     std::vector<int> h_it(NP, 0), h_conv(NP, 1), h_dinfo(4 * P, 0), init(NP, 0);
@@ -1558,7 +2029,10 @@ int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, con
       if (!accepted[p]) { init[2 * p + side] = 1; any = true; }
     if (any) {
       h->plan_error = false;
-      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd, true);
+      // the accepted seeds keep their g in es[side]; the other lead is not needed
+      std::vector<int> skip(NP, 0);
+      for (int p = 0; p < P; ++p) { skip[2 * p + side] = accepted[p]; skip[2 * p + 1 - side] = 1; }
+      build_decimation(h, pts, act, itr, conv, dinfo, na, nb, nd, true, &skip);
       // g = es^-1 for the lead: [es | 1] -> LU
       Plan& F = h->p_final_g;
       F.clear();

@@ -100,7 +100,7 @@ struct Norm1Desc {
   const int* active;
 };
 
-struct TraceDesc {  // out = sum_{a,b} A[a,b] * B[b,a]
+struct TraceDesc {  // out = sum_{a,b} A[a,b] * B[b,a]; b == nullptr: out = sum_a A[a,a]
   const z64* a; int lda;
   const z64* b; int ldb;
   int n;
@@ -150,6 +150,8 @@ namespace ss {
 cudaStream_t mlp_stream(const ss_mlp* n);
 void mlp_dims(const ss_mlp* n, int* n_in, int* n_out, int* max_batch);
 void launch_real_part(const z64* in, double* out, int n, cudaStream_t st);
+// out[i] = scale * Im(in[i])
+void launch_scaled_imag(const z64* in, double* out, int n, double scale, cudaStream_t st);
 // out += sum |a|^2 (Norm1Desc reused; *out must start at 0)
 void launch_frob2(const Norm1Desc* d, int nprob, int max_cols, cudaStream_t st);
 void launch_unpack_g(const float* y, int s, double inv_scale, z64* g, int ldg, cudaStream_t st);

@@ -5,7 +5,8 @@
 //          z = E + i eta, right-hand sides, copies, Gamma = i(Sigma - Sigma^H).
 //  norm1   max column sum of |a_ij| (the doubling's stopping test).
 //  trace   sum_{a,b} A[a,b] B[b,a] = Tr[A B], the transmission reduction
-//          (deterministic tree; one CTA per problem).
+//          (deterministic tree; one CTA per problem), or Tr[A] (density of
+//          states).
 #include "ss_internal.cuh"
 
 namespace ss {
@@ -114,10 +115,15 @@ __global__ void __launch_bounds__(RNT) trace_kernel(const TraceDesc* __restrict_
   const TraceDesc d = descs[blockIdx.x];
   if (d.active && __ldg(d.active) == 0) return;
   // thread t sums rows a = t, t + RNT, ...; for each a it walks b.
+  // b == nullptr: the trace of A itself (sum of its diagonal).
   z64 acc = zmk(0.0, 0.0);
-  for (int a = threadIdx.x; a < d.n; a += RNT) {
-    for (int b = 0; b < d.n; ++b) {
-      zfma(acc, d.a[(size_t)a * d.lda + b], d.b[(size_t)b * d.ldb + a]);
+  if (!d.b) {
+    for (int a = threadIdx.x; a < d.n; a += RNT) acc = zadd(acc, d.a[(size_t)a * d.lda + a]);
+  } else {
+    for (int a = threadIdx.x; a < d.n; a += RNT) {
+      for (int b = 0; b < d.n; ++b) {
+        zfma(acc, d.a[(size_t)a * d.lda + b], d.b[(size_t)b * d.ldb + a]);
+      }
     }
   }
   __shared__ z64 red[RNT / 32];
@@ -190,6 +196,11 @@ __global__ void real_part_kernel(const z64* __restrict__ in, double* __restrict_
   if (i < n) out[i] = in[i].x;
 }
 
+__global__ void scaled_imag_kernel(const z64* __restrict__ in, double* __restrict__ out, int n, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = scale * in[i].y;
+}
+
 __global__ void fill_i32_kernel(int* p, int n, int v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -209,6 +220,11 @@ void launch_unpack_g(const float* y, int s, double inv_scale, z64* g, int ldg, c
 void launch_real_part(const z64* in, double* out, int n, cudaStream_t st) {
   if (n <= 0) return;
   real_part_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+}
+
+void launch_scaled_imag(const z64* in, double* out, int n, double scale, cudaStream_t st) {
+  if (n <= 0) return;
+  scaled_imag_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n, scale);
 }
 
 void launch_fill_i32(int* p, int n, int v, cudaStream_t st) {

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import dense
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -122,5 +123,89 @@ def test_warm_start_workload_report(ss, capsys):
                   mean_iters_warm=float(np.where(acc, it1, it0 + 8).mean()), t_plain_s=round(t_plain, 3),
                   t_warm_s=round(t_warm, 3), gain_time=round(t_plain / t_warm, 3))
     with capsys.disabled():
-        print("\nwarm-start report:", report)
+        print("\nwarm-start report (in band):", report)
     assert losses[-1] < losses[0]
+
+
+def test_warm_start_gap_energies_report(ss, capsys):
+    """The same lead (s_b = 128) at energies in the gap above its band, where
+    every mode decays and the fixed point contracts by |lambda|^2 < 1: a
+    network trained there (1024 points) seeds 512 evaluation energies.  Reports
+    accepted seeds and time against the plain doubling; checks that every
+    accepted g equals the doubling's within the residual bar."""
+    import torch
+    from paper_1812_01396_gb300 import warm
+    s = 128
+    dev = synth.make_device(2, s, seed=5)[0]
+    h = ss.Handle(n_b_max=2, s_b_max=s, max_points=64, max_inj=1)
+    try:
+        h.set_device(0, dev)
+        rng = np.random.default_rng(9)
+        Etr = rng.uniform(40.0, 60.0, 1024)
+        g_probe, _, _, _, _ = h.surface_gf(Etr[:64], np.zeros(64, np.int32), side=1)
+        scale = 1.0 / float(np.sqrt(np.mean([np.mean(np.abs(g) ** 2) for g in g_probe])))
+        net = ss.MLP(warm.N_IN, 512, 2 * s * s, 256, seed=12)
+        losses, _ = warm.train(net, h, Etr, np.zeros(1024, np.int32), np.zeros(1024), 1, scale, epochs=30,
+                               batch=256, lr=1e-3)
+        h.set_warm_start(net, 1, scale)
+        Ev = np.linspace(41.0, 59.0, 512)
+        kid = np.zeros(512, np.int32)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
+        t_plain = time.time() - t0
+        t0 = time.time()
+        g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(512), side=1, use_warm=True, warm_iters=8,
+                                               warm_tol=1e-10)
+        t_warm = time.time() - t0
+    finally:
+        h.close()
+    errs = np.array([rel(a, b) for a, b in zip(g1, g0)])
+    acc = seeded.astype(bool)
+    assert np.all(np.asarray(st0) == 0) and np.all(np.asarray(st1) == 0)
+    assert np.all(errs[~acc] == 0.0)
+    if acc.any():
+        assert np.max(errs[acc]) < 1e-9, np.max(errs[acc])
+    report = dict(train_points=1024, final_loss=losses[-1], first_loss=losses[0], eval_points=512,
+                  accepted=int(acc.sum()), mean_iters_plain=float(it0.mean()), t_plain_s=round(t_plain, 3),
+                  t_warm_s=round(t_warm, 3), gain_time=round(t_plain / t_warm, 3))
+    with capsys.disabled():
+        print("\nwarm-start report (gap):", report)
+
+
+def test_pipeline_warm_start_accepted_branch(ss):
+    """cfg.warm_start inside ss_self_energy / ss_solve: at energies far above the
+    band the fixed point contracts by about |lambda|^2 ~ 0.02 per step, so even
+    an untrained network's seed (scaled down) passes the 1e-10 Dyson test
+    after 8 steps; those leads skip the doubling (iters = -8) and their
+    self-energies, T and x must still equal the oracle's.  The in-band point
+    is rejected and equals the run without warm start bit for bit."""
+    import torch
+    dev = synth.make_device(4, 32, seed=21)[0]
+    net = ss.MLP(19, 64, 2 * 32 * 32, 8, seed=5)
+    Es = [60.0, 0.3, 75.0]
+    inj = [synth.make_injection(32, 2, seed=30 + i)[0] for i in range(3)]
+    out = {}
+    for ws in (0, 1):
+        h = ss.Handle(n_b_max=4, s_b_max=32, max_points=3, max_inj=2, warm_start=ws)
+        try:
+            h.set_device(0, dev)
+            h.set_momentum(0, 0.0)
+            h.set_warm_start(net, 0, 1e3)
+            h.set_warm_start(net, 1, 1e3)
+            sL, sR, it, st, _ = h.self_energy(Es, [0, 0, 0])
+            xs, stx, _ = h.solve(Es, [0, 0, 0], inj)
+            T, err, stT, _ = h.transmission(Es, [0, 0, 0])
+        finally:
+            h.close()
+        out[ws] = dict(sL=sL, sR=sR, it=np.asarray(it), x=xs, T=np.asarray(T), st=np.asarray(stT))
+    w, p0 = out[1], out[0]
+    assert np.all(w["st"] == 0)
+    assert list(w["it"][0]) == [-8, -8] and list(w["it"][2]) == [-8, -8], w["it"]
+    assert np.all(w["it"][1] > 0)
+    assert np.array_equal(w["sL"][1], p0["sL"][1]) and float(w["T"][1]) == float(p0["T"][1])
+    for p in (0, 2):
+        ref = dense.solve_point(dev, Es[p], inj[p])
+        assert rel(w["sL"][p], ref["sigma_L"]) < 1e-9 and rel(w["sR"][p], ref["sigma_R"]) < 1e-9
+        assert rel(w["x"][p], ref["x"]) < 1e-9
+        assert dense.rel_T_err(float(w["T"][p]), ref["T"]) < 1e-10

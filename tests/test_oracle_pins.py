@@ -432,3 +432,30 @@ def test_open_channels_of_decoupled_wire_closed_form():
         expect = int(np.sum(np.abs(E - eps) < 2 * abs(t)))
         m, n_unit = channels.open_channels(cell, E)
         assert m == expect and n_unit == 2 * expect
+
+
+# ------------------------------------------------------- density of states
+@pytest.mark.parametrize("k", [0.4, 1.3, 2.5])
+def test_ldos_of_perfect_chain_closed_form(k):
+    """A perfect 1-D chain (device cells equal to the lead cells): every site
+    carries the bulk density of states 1 / (pi sqrt(4 t^2 - (E - eps0)^2)) in band."""
+    eps0, t = 0.2, -0.7
+    E = eps0 + 2 * t * math.cos(k)
+    rho = dense.ldos(chain_device(eps0, t, n_b=5), E)
+    expect = 1.0 / (math.pi * math.sqrt(4 * t * t - (E - eps0) ** 2))
+    assert np.allclose(rho, expect, rtol=1e-8, atol=0)
+
+
+def test_ldos_of_decoupled_wire_closed_form():
+    """Decoupled wire: the trace is basis independent, so each cell's LDOS is the
+    sum of the 1-D bulk densities of the chains whose band holds E (zero in gaps)."""
+    s, t = 8, -0.8
+    dev, eps = synth.decoupled_wire(s, 4, t, seed=6)
+    for E in (-1.9, -0.3, 0.6, 2.2):
+        edges = np.concatenate([eps - 2 * abs(t), eps + 2 * abs(t)])
+        if np.min(np.abs(E - edges)) < 0.05:
+            continue
+        inb = np.abs(E - eps) < 2 * abs(t)
+        expect = float(np.sum(1.0 / (np.pi * np.sqrt(4 * t * t - (E - eps[inb]) ** 2))))
+        rho = dense.ldos(dev, E)
+        assert np.allclose(rho, expect, rtol=1e-7, atol=1e-9), (E, rho, expect)
