@@ -526,6 +526,7 @@ def main():
                 step(h, s_, inj_dev)
         stream.synchronize()
         launches0 = h.launch_count()
+        host0 = h.host_launch_count()
         iters, Ts, sts, errs = [], [], [], []
         barrier()
         torch.cuda.synchronize()
@@ -547,6 +548,7 @@ def main():
         torch.cuda.synchronize()
         t = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
         launches = h.launch_count() - launches0
+        host_calls = h.host_launch_count() - host0
         h.close()
         flops = sum(point_flops(a.n_b, a.s_b, a.n_inj, int(it[p, 0]), int(it[p, 1])) for it in iters for p in range(P))
         hp = handle(prec, profile=1)
@@ -562,6 +564,7 @@ def main():
             kern[name] = {"ms": ms, "launches": n, "flops": fl, "issued": hp.profile_issued(name)}
         hp.close()
         return dict(t=t, value=P * steps * world / t, tflops=flops * world / t / 1e12, kern=kern, launches=launches,
+                    host_calls_per_step=host_calls / steps,
                     T=np.concatenate(Ts), ok=bool(np.all(np.concatenate(sts) == 0)), steps=steps,
                     status=np.concatenate(sts), err=np.concatenate(errs))
 
@@ -696,6 +699,7 @@ def main():
             "T_vs_oracle": vs_oracle,
             "e2e": e2e,
             "gpu_launches": head["launches"],
+            "host_launch_calls_per_step": head["host_calls_per_step"],
             "clocks": clk.summary(),
             "lu_tune": {("fp64" if k == ss.SS_FP64 else "mixed"): {"panel_width": v[0], "outer_width": v[1],
                                                                   "update": v[2], "ms": v[3]}

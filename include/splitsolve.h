@@ -63,6 +63,11 @@ typedef struct ss_handle ss_handle;
                                exact FP32 accumulation (FP64-accurate); FP64 panels,
                                pivoting, boundary solve and residual                     */
 
+/* open-boundary (lead self-energy) methods */
+#define SS_OBC_DECIMATION 0  /* Sancho-Rubio doubling of the surface Green's function   */
+#define SS_OBC_FEAST      1  /* the leads' Bloch modes from a contour integral (Sec. 3A,
+                                Eq. feast) with a Rayleigh-Ritz step, Sigma from them   */
+
 typedef struct {
   int n_b_max;        /* largest n_b of any k_id (workspace sizing)                   */
   int s_b_max;        /* largest s_b of any k_id                                      */
@@ -97,6 +102,26 @@ typedef struct {
                          (2 n_b + 45) s_b^2 in FP64 with one partition.  Calls that
                          return wave functions or the density of states then fit fewer
                          points per batch, or fail with SS_ERR_OOM.  Default 0.        */
+  int hermitian_sweeps; /* 1: factor the sweep blocks D_i = A_ii - A_{i,i+1} X_{i+1}
+                         (Hermitian at real E) as L D L^H without pivoting, the
+                         paper's no-pivoting Hermitian solver (Sec. 5E): only their
+                         lower triangle is updated, half the factorisation work of
+                         the pivoted LU.  A zero pivot gives SS_ERR_SINGULAR.
+                         Default 0 (pivoted LU).                                      */
+  int obc;            /* SS_OBC_DECIMATION (default) or SS_OBC_FEAST: the leads' modes
+                         psi_q = lambda^q u of (L + lambda D + lambda^2 U) u = 0 (blocks of
+                         z S - H at z = E + i*eta) inside the annulus 1/R < |lambda| < R,
+                         from 2*feast_points contour solves (z B - A)^-1 B Y on |z| = R
+                         and |z| = 1/R (one batched s_b x s_b LU each), an orthonormal
+                         basis of the filtered subspace and a Rayleigh-Ritz step; the
+                         modes going into the bulk (|lambda| < 1 right lead, > 1 left)
+                         give F = U diag(lambda) U^+ and g = (D + U F)^-1 (right) or
+                         (D + L F)^-1 (left), dropping modes outside the annulus (exact
+                         when it holds all s_b of them).  Needs s_b <= 256 (subspace
+                         up to 512).  Iteration counts are reported as 0.           */
+  double feast_radius;/* R > 1 (default 50)                                               */
+  int feast_points;   /* quadrature nodes per circle (default 16)                        */
+  int feast_subspace; /* columns m0 of the random block Y (0 = 2 s_b, the full space)   */
 } ss_config;
 
 /* Fill *cfg with the defaults listed above (n_b_max = 64, s_b_max = 512,
@@ -181,6 +206,13 @@ const char* ss_last_error(const ss_handle* h);
 /* Number of kernel launches the library issued on this handle since
  * ss_create (graph replays count their kernel nodes). */
 long long ss_launch_count(const ss_handle* h);
+
+/* Host-side launch calls the pipeline calls (ss_self_energy, ss_solve,
+ * ss_transmission, ss_dos) made on this handle since ss_create: one per eager
+ * kernel launch or memset, one per CUDA-graph launch.  A plan whose launch
+ * sequence repeats (same shapes and batch as before) is replayed from a graph
+ * when cfg.use_graphs = 1. */
+long long ss_host_launch_count(const ss_handle* h);
 
 /* Complex GEMM with the library's kernels: C = op(A) op(B), op = identity or
  * conjugate transpose (transA / transB = 1), all DEVICE pointers, row-major
@@ -329,6 +361,8 @@ int ss_surface_gf(ss_handle* h, int n_pts, const double* E, const int* k_id, con
 #define SS_KERNEL_FROB2     16  /* Frobenius norms (warm-start judge, refinement)     */
 #define SS_KERNEL_ZGEMM_LU  17  /* SS_KERNEL_ZGEMM launches issued by the block LU    */
 #define SS_KERNEL_OZGEMM_LU 18  /* SS_KERNEL_OZGEMM launches issued by the block LU   */
+#define SS_KERNEL_LU_HPANEL 19  /* Hermitian LDL^H panel (cfg.hermitian_sweeps)      */
+#define SS_KERNEL_EIG       20  /* small dense eigenproblems (SS_OBC_FEAST)           */
 
 /* With cfg.profile = 1: total device time (ms, CUDA events around each
  * launch on cfg.stream), algorithmic flops (GEMM kind only: 8 m n k per

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libsplitsolve.so")
 SS_OK, SS_ERR_ARG, SS_ERR_STATE, SS_ERR_SINGULAR, SS_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 SS_ERR_TIMEOUT, SS_ERR_OOM, SS_ERR_CUDA = 5, 6, 7
 SS_FP64, SS_MIXED_BF16X3, SS_MIXED_BF16X6, SS_MIXED_OZAKI = 0, 1, 2, 3
+SS_OBC_DECIMATION, SS_OBC_FEAST = 0, 1
 STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_STATE", 3: "SS_ERR_SINGULAR",
                 4: "SS_ERR_NOT_CONVERGED", 5: "SS_ERR_TIMEOUT", 6: "SS_ERR_OOM", 7: "SS_ERR_CUDA"}
 
@@ -32,10 +33,11 @@ EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_ener
            "ss_caroli_transmission_noalloc", "ss_noalloc_last_error", "ss_mlp_create", "ss_mlp_destroy",
            "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward", "ss_mlp_train_step", "ss_mlp_last_error",
            "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan", "ss_dos",
-           "ss_set_momentum")
+           "ss_set_momentum", "ss_host_launch_count")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
                 "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
-                "oz_scale": 13, "oz_pack": 14, "ozgemm": 15, "frob2": 16, "zgemm_lu": 17, "ozgemm_lu": 18}
+                "oz_scale": 13, "oz_pack": 14, "ozgemm": 15, "frob2": 16, "zgemm_lu": 17, "ozgemm_lu": 18,
+                "lu_hpanel": 19, "eig": 20}
 
 
 class SSConfig(C.Structure):
@@ -45,6 +47,8 @@ class SSConfig(C.Structure):
         ("decim_max_iter", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
         ("warm_start", C.c_int), ("stream", C.c_void_p), ("device_ptrs", C.c_int),
         ("use_graphs", C.c_int), ("profile", C.c_int), ("partitions", C.c_int), ("memory_lean", C.c_int),
+        ("hermitian_sweeps", C.c_int), ("obc", C.c_int), ("feast_radius", C.c_double),
+        ("feast_points", C.c_int), ("feast_subspace", C.c_int),
     ]
 
 
@@ -80,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.ss_last_error.restype = C.c_char_p
     lib.ss_launch_count.argtypes = [vp]
     lib.ss_launch_count.restype = C.c_longlong
+    lib.ss_host_launch_count.argtypes = [vp]
+    lib.ss_host_launch_count.restype = C.c_longlong
     lib.ss_profile_read.argtypes = [vp, C.c_int, dp, dp, C.POINTER(C.c_longlong)]
     lib.ss_profile_read.restype = C.c_int
     lib.ss_profile_read_issued.argtypes = [vp, C.c_int, dp]
@@ -190,6 +196,10 @@ class Handle:
 
     def launch_count(self) -> int:
         return int(self._lib.ss_launch_count(self._h))
+
+    def host_launch_count(self) -> int:
+        """ss_host_launch_count: host-side launch calls (eager kernels, memsets, graph launches)."""
+        return int(self._lib.ss_host_launch_count(self._h))
 
     def profile_read(self, kind):
         """(total_ms, flops, launches) of one kernel kind (needs profile=1)."""

@@ -303,6 +303,13 @@ struct ss_handle {
   bool c_sigma = false, c_T = false;
   std::vector<double> cT, cTi;
   std::vector<int> c_iters, c_status;
+  long long nhost = 0;  // host-side launch calls (eager kernels, memsets, graph launches)
+  // contour-integral (FEAST) open boundary conditions: scratch and plans
+  char* feast_buf = nullptr;
+  size_t feast_bytes = 0;
+  int* feast_info = nullptr;
+  size_t feast_info_n = 0;
+  Plan p_fa, p_fb, p_fc;
 };
 
 namespace {
@@ -339,6 +346,14 @@ void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
   auto it = h->tune.find(smax);
   if (it != h->tune.end()) { nb = it->second.nb; nbo = it->second.nbo; upd = (Plan::Updates)it->second.upd; }
   if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo)) h->plan_error = true;
+}
+// The sweep blocks D_i with cfg.hermitian_sweeps: LDL^H without pivoting,
+// updates on the lower triangle (FP64 path: FP64 updates of depth 16; mixed
+// path: exact tensor-core updates of depth 32).
+void ldl(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
+  const bool mx = h->mixed();
+  if (!P.ldl_solve(ds, mx ? 32 : 16, mx ? Plan::UPD_EXACT_TC : Plan::UPD_FP64, h->pack, h->pack_bytes, h->tc_err))
+    h->plan_error = true;
 }
 
 // ---------------------------------------------------------- self-energies
@@ -701,7 +716,9 @@ void build_sweeps(ss_handle* h, std::vector<PW>& pts, int* info, int nsteps, boo
     }
     big_gemm(h, S, g);
     S.form(f);
-    ::lu(h, S, lu);
+    // D_i is Hermitian at real E (a Schur complement of the Hermitian A)
+    if (h->cfg.hermitian_sweeps) ::ldl(h, S, lu);
+    else ::lu(h, S, lu);
     S.form(fc);
   }
   for (auto& w : pts) {
@@ -1158,6 +1175,412 @@ void build_dos_diag(ss_handle* h, std::vector<PW>& pts, int* info, z64* traces, 
   }
 }
 
+// ------------------------------------------- contour-integral (FEAST) leads
+// Sec. 3A, Eq. bound and Eq. feast: the lead's Bloch modes psi_q = lambda^q u
+// solve (L + lambda D + lambda^2 U) u = 0 (blocks of z S - H at z = E + i eta;
+// companion form A v = lambda B v, v = [u; lambda u], A = [[0, 1], [-L, -D]],
+// B = [[1, 0], [0, U]]).  Per (point, lead):
+//   1. contour solves: X_p = (z_p B - A)^-1 B Y at 2 Np nodes on |z| = R
+//      (counterclockwise) and |z| = 1/R (clockwise), Y a fixed 2s x m0 random
+//      block; by the block form of z B - A each is one s x s solve,
+//      (L + z D + z^2 U) X1 = U (Y2 + z Y1) + D Y1, X2 = z X1 - Y1, all
+//      nodes of all problems in one batched LU;
+//   2. Q = sum_p (z_p / Np) X_p (minus on the inner circle): the spectral
+//      projector onto the annulus 1/R < |lambda| < R applied to Y;
+//   3. an orthonormal basis of span Q: eigen-decomposition of the Gram matrix
+//      Q^H Q, directions with singular value below 1e-10 of the largest dropped;
+//   4. Rayleigh-Ritz: K = (Qt^H B Qt)^-1 (Qt^H A Qt), its eigenpairs (ss_eig.cu),
+//      u_j = first half of Qt y_j;
+//   5. on the host: the modes inside the annulus going towards the bulk (right
+//      lead |lambda| < 1, left lead |lambda| > 1);
+//   6. F = U_m diag(f) U_m^+ (f = lambda, or 1/lambda on the left; U_m^+ = U_m^-1
+//      when all s modes are found, (U_m^H U_m)^-1 U_m^H otherwise), the surface
+//      Green's function g = (D + U F)^-1 (right) or (D + L F)^-1 (left), and
+//      Sigma = A_{n,n+1} g A_{n+1,n} / A_{1,0} g A_{0,1} at real E.
+struct FeastProb {
+  PW* w;
+  int q;       // lead: 0 left, 1 right
+  int s, m0;   // block size, subspace columns
+  int k = 0;   // rank kept after the Gram step
+  int mm = 0;  // modes used for F
+  // scratch (device)
+  z64 *Y, *Wn, *Tn, *Q, *G, *GZ, *GX, *Glam, *Qt, *AQ, *RR, *KZ, *KX, *Klam, *ZX, *Ua, *Ut, *Uf, *PS, *PF, *GG, *F;
+  int *piv, *pivn, *info;
+};
+
+size_t feast_prob_bytes(int s, int m0, int np2) {
+  Carve c(nullptr);
+  FeastProb f{};
+  f.s = s; f.m0 = m0;
+  const size_t sm = (size_t)s * m0, mm2 = (size_t)m0 * m0;
+  c.take<z64>(2 * sm); c.take<z64>((size_t)np2 * s * (s + m0)); c.take<z64>((size_t)np2 * sm); c.take<z64>(2 * sm);
+  for (int i = 0; i < 3; ++i) c.take<z64>(mm2);
+  c.take<z64>(m0); c.take<z64>(2 * sm); c.take<z64>(2 * sm); c.take<z64>((size_t)m0 * 2 * m0);
+  for (int i = 0; i < 3; ++i) c.take<z64>(mm2);
+  c.take<z64>(m0); c.take<z64>(sm); c.take<z64>(sm); c.take<z64>(sm); c.take<z64>(sm);
+  const size_t ps = (size_t)m0 * std::max(m0, s);
+  c.take<z64>(ps); c.take<z64>(ps); c.take<z64>((size_t)m0 * (m0 + 2 * s)); c.take<z64>((size_t)s * s);
+  c.take<int>((size_t)np2 * s); c.take<int>(2 * m0 + 2 * s);
+  return c.off + 256;
+}
+
+void feast_carve(Carve& c, FeastProb& f, int np2) {
+  const int s = f.s, m0 = f.m0;
+  const size_t sm = (size_t)s * m0, mm2 = (size_t)m0 * m0;
+  f.Y = c.take<z64>(2 * sm); f.Wn = c.take<z64>((size_t)np2 * s * (s + m0)); f.Tn = c.take<z64>((size_t)np2 * sm);
+  f.Q = c.take<z64>(2 * sm);
+  f.G = c.take<z64>(mm2); f.GZ = c.take<z64>(mm2); f.GX = c.take<z64>(mm2); f.Glam = c.take<z64>(m0);
+  f.Qt = c.take<z64>(2 * sm); f.AQ = c.take<z64>(2 * sm); f.RR = c.take<z64>((size_t)m0 * 2 * m0);
+  f.KZ = c.take<z64>(mm2); f.KX = c.take<z64>(mm2); f.ZX = c.take<z64>(mm2); f.Klam = c.take<z64>(m0);
+  f.Ua = c.take<z64>(sm); f.Ut = c.take<z64>(sm); f.Uf = c.take<z64>(sm); f.AQ = f.AQ;
+  c.take<z64>(sm);
+  const size_t ps = (size_t)m0 * std::max(m0, s);
+  f.PS = c.take<z64>(ps); f.PF = c.take<z64>(ps); f.GG = c.take<z64>((size_t)m0 * (m0 + 2 * s));
+  f.F = c.take<z64>((size_t)s * s);
+  f.pivn = c.take<int>((size_t)np2 * s); f.piv = c.take<int>(2 * m0 + 2 * s);
+}
+
+// Seeded complex Gaussian-like block (a 64-bit LCG; the subspace only has to
+// be generic), the same for every problem of a given shape.
+std::vector<z64> feast_random_block(int rows, int cols) {
+  std::vector<z64> y((size_t)rows * cols);
+  unsigned long long r = 0x9E3779B97F4A7C15ull ^ ((unsigned long long)rows << 32) ^ (unsigned long long)cols;
+  for (auto& v : y) {
+    r = r * 6364136223846793005ull + 1442695040888963407ull;
+    const double a = ((double)((r >> 11) & ((1ull << 52) - 1)) / (double)(1ull << 52)) - 0.5;
+    r = r * 6364136223846793005ull + 1442695040888963407ull;
+    const double b = ((double)((r >> 11) & ((1ull << 52) - 1)) / (double)(1ull << 52)) - 0.5;
+    v = make_double2(a, b);
+  }
+  return y;
+}
+
+z64 zinv_host(z64 a) {
+  const double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+
+int run_feast(ss_handle* h, std::vector<PW>& pts) {
+  cudaStream_t st = h->stream;
+  const int P = (int)pts.size();
+  const int np = h->cfg.feast_points;
+  const int np2 = 2 * np;
+  const double Rr = h->cfg.feast_radius, eta = h->cfg.eta;
+  std::vector<FeastProb> fp;
+  size_t bytes = 0;
+  for (auto& w : pts)
+    for (int q = 0; q < 2; ++q) {
+      FeastProb f{};
+      f.w = &w; f.q = q; f.s = w.s;
+      f.m0 = h->cfg.feast_subspace > 0 ? std::min(h->cfg.feast_subspace, 2 * w.s) : 2 * w.s;
+      bytes += feast_prob_bytes(f.s, f.m0, np2);
+      fp.push_back(f);
+    }
+  if (bytes > h->feast_bytes) {
+    cudaFree(h->feast_buf);
+    h->feast_buf = nullptr; h->feast_bytes = 0;
+    CK(cudaMalloc(&h->feast_buf, bytes), "contour-integral scratch");
+    h->feast_bytes = bytes;
+  }
+  Carve c(h->feast_buf);
+  for (auto& f : fp) feast_carve(c, f, np2);
+  if (h->feast_info_n < 8 * fp.size()) {
+    cudaFree(h->feast_info);
+    h->feast_info = nullptr; h->feast_info_n = 0;
+    CK(cudaMalloc(&h->feast_info, sizeof(int) * 8 * fp.size()), "contour-integral flags");
+    h->feast_info_n = 8 * fp.size();
+  }
+  for (size_t i = 0; i < fp.size(); ++i) fp[i].info = h->feast_info + 8 * i;
+  // random blocks Y (host, uploaded)
+  for (auto& f : fp) {
+    const std::vector<z64> y = feast_random_block(2 * f.s, f.m0);
+    CK(cudaMemcpyAsync(f.Y, y.data(), y.size() * sizeof(z64), cudaMemcpyHostToDevice, st), "feast Y");
+  }
+  // ---------------- plan A: lead blocks, contour solves, Q, Gram matrix, its eigenpairs
+  Plan& A = h->p_fa;
+  A.clear();
+  {
+    std::vector<FormDesc> f0, f1;
+    std::vector<std::vector<FormDesc>> qpass;  // per problem: the running-sum passes, then the Y1 term
+    std::vector<GemmDesc> g1, g2, gG;
+    std::vector<LuDesc> lu;
+    std::vector<EigDesc> eg;
+    for (auto& f : fp) {
+      PW& w = *f.w;
+      const int s = f.s, m0 = f.m0, q = f.q;
+      const z64 z = make_double2(w.E, eta);
+      const z64* const* cc = w.kd->cell[q];
+      z64 *D = w.D[q], *U = w.a[q][0], *L = w.b[q][0];
+      f0.push_back(fformed(D, s, cc[2], cc[0], z, s, s, s));
+      f0.push_back(fformed(U, s, cc[3], cc[1], z, s, s, s));
+      f0.push_back(fformed(L, s, cc[3], cc[1], z, s, s, s, 1));
+      const z64* Y1 = f.Y;
+      const z64* Y2 = f.Y + (size_t)s * m0;
+      for (int p = 0; p < np2; ++p) {
+        const bool outer = p < np;
+        const double rad = outer ? Rr : 1.0 / Rr, th = 2.0 * M_PI * ((p % np) + 0.5) / np;
+        const z64 zp = make_double2(rad * std::cos(th), rad * std::sin(th));
+        const z64 zp2 = zmul(zp, zp);
+        z64* W = f.Wn + (size_t)p * s * (s + m0);
+        const int ld = s + m0;
+        // P(z) = L + z D + z^2 U
+        FormDesc pz = fdesc(W, ld, s, s);
+        pz.x = L; pz.ldx = s; pz.ax = ONE;
+        pz.y = D; pz.ldy = s; pz.ay = zp;
+        pz.z = U; pz.ldz = s; pz.az = zp2;
+        f1.push_back(pz);
+        // T = Y2 + z Y1 ; rhs = U T + D Y1
+        z64* T = f.Tn + (size_t)p * s * m0;
+        FormDesc tf = fdesc(T, m0, s, m0);
+        tf.x = Y2; tf.ldx = m0; tf.ax = ONE;
+        tf.y = Y1; tf.ldy = m0; tf.ay = zp;
+        f1.push_back(tf);
+        g1.push_back(gdesc(s, m0, s, plain(U, s), plain(T, m0), W + s, ld, ONE, ZERO));
+        g2.push_back(gdesc(s, m0, s, plain(D, s), plain(Y1, m0), W + s, ld, ONE, ONE));
+        LuDesc Ld{};
+        Ld.w = W; Ld.ldw = ld; Ld.s = s; Ld.ncols = s + m0; Ld.ipiv = f.pivn + (size_t)p * s; Ld.info = f.info;
+        lu.push_back(Ld);
+      }
+      // Q1 = sum_p c_p X1_p, Q2 = sum_p c_p (z_p X1_p - Y1): c_p = +z_p / Np outer,
+      // -z_p / Np inner; three nodes per form pass (terms x, y, z; v carries the
+      // running sum), passes of one problem in consecutive launches
+      z64* Q1 = f.Q;
+      z64* Q2 = f.Q + (size_t)s * m0;
+      z64 csum = ZERO;
+      std::vector<FormDesc> mine;
+      for (int p0 = 0; p0 < np2; p0 += 3) {
+        FormDesc a1 = fdesc(Q1, m0, s, m0), a2 = fdesc(Q2, m0, s, m0);
+        const z64* src[3] = {nullptr, nullptr, nullptr};
+        z64 co[3], co2[3];
+        for (int t = 0; t < 3; ++t) {
+          const int p = p0 + t;
+          if (p >= np2) break;
+          const bool outer = p < np;
+          const double rad = outer ? Rr : 1.0 / Rr, th = 2.0 * M_PI * ((p % np) + 0.5) / np;
+          const z64 zp = make_double2(rad * std::cos(th), rad * std::sin(th));
+          const z64 cp = make_double2((outer ? 1.0 : -1.0) * zp.x / np, (outer ? 1.0 : -1.0) * zp.y / np);
+          src[t] = f.Wn + (size_t)p * s * (s + m0) + s;
+          co[t] = cp;
+          co2[t] = zmul(cp, zp);
+          csum = zadd(csum, cp);
+        }
+        a1.x = src[0]; a1.ldx = s + m0; a1.ax = co[0];
+        a2.x = src[0]; a2.ldx = s + m0; a2.ax = co2[0];
+        if (src[1]) { a1.y = src[1]; a1.ldy = s + m0; a1.ay = co[1]; a2.y = src[1]; a2.ldy = s + m0; a2.ay = co2[1]; }
+        if (src[2]) { a1.z = src[2]; a1.ldz = s + m0; a1.az = co[2]; a2.z = src[2]; a2.ldz = s + m0; a2.az = co2[2]; }
+        if (p0 > 0) { a1.v = Q1; a1.ldv = m0; a1.av = ONE; a2.v = Q2; a2.ldv = m0; a2.av = ONE; }
+        mine.push_back(a1);
+        mine.push_back(a2);
+      }
+      // the -Y1 terms of Q2: - (sum_p c_p) Y1
+      FormDesc fy = fcopy(Q2, m0, Q2, m0, s, m0);
+      fy.y = Y1; fy.ldy = m0; fy.ay = make_double2(-csum.x, -csum.y);
+      mine.push_back(fy);
+      qpass.push_back(mine);
+      // Gram matrix Q^H Q = Q1^H Q1 + Q2^H Q2
+      gG.push_back(gdesc(m0, m0, s, plain(Q1, m0, 1), plain(Q1, m0), f.G, m0, ONE, ZERO));
+      gG.push_back(gdesc(m0, m0, s, plain(Q2, m0, 1), plain(Q2, m0), f.G, m0, ONE, ONE));
+      eg.push_back({f.G, f.GZ, f.GX, f.Glam, m0, m0, f.info + 1});
+    }
+    A.memset0(h->feast_info, sizeof(int) * h->feast_info_n);
+    A.form(f0);
+    A.form(f1);
+    A.gemm(g1);
+    A.gemm(g2);
+    ::lu(h, A, lu);
+    // the passes of one problem are sequential (running sums): one launch per pass index
+    const size_t npass = qpass.empty() ? 0 : qpass[0].size();
+    for (size_t k = 0; k + 1 < npass; k += 2) {
+      std::vector<FormDesc> one;
+      for (auto& v : qpass) { one.push_back(v[k]); one.push_back(v[k + 1]); }
+      A.form(one);
+    }
+    std::vector<FormDesc> last;
+    for (auto& v : qpass) last.push_back(v.back());
+    A.form(last);
+    A.gemm(gG);
+    A.eig(eg);
+  }
+  CK(A.upload(st), "upload feast A");
+  CK(A.run(st, &h->nlaunch, h->P()), "feast contour solves");
+  // ---------------- host: rank of Q from the Gram eigenvalues
+  std::vector<std::vector<z64>> glam(fp.size());
+  for (size_t i = 0; i < fp.size(); ++i) {
+    glam[i].resize(fp[i].m0);
+    CK(cudaMemcpyAsync(glam[i].data(), fp[i].Glam, sizeof(z64) * fp[i].m0, cudaMemcpyDeviceToHost, st), "gram");
+  }
+  std::vector<int> finfo(h->feast_info_n);
+  CK(cudaMemcpyAsync(finfo.data(), h->feast_info, sizeof(int) * finfo.size(), cudaMemcpyDeviceToHost, st), "info");
+  CK(cudaStreamSynchronize(st), "feast sync");
+  for (size_t i = 0; i < fp.size(); ++i) {
+    FeastProb& f = fp[i];
+    if (finfo[(i * 8)] || finfo[i * 8 + 1]) return fail(h, SS_ERR_SINGULAR, "contour-integral solve failed (singular node or eigen-iteration cap)");
+    double mx = 0.0;
+    for (auto& v : glam[i]) mx = std::max(mx, v.x);
+    std::vector<z64> S((size_t)f.m0 * f.m0, ZERO);
+    int k = 0;
+    for (int j = 0; j < f.m0; ++j)
+      if (glam[i][j].x > 1e-20 * mx) { S[(size_t)j * f.m0 + k] = make_double2(1.0 / std::sqrt(glam[i][j].x), 0.0); ++k; }
+    f.k = k;
+    CK(cudaMemcpyAsync(f.PS, S.data(), S.size() * sizeof(z64), cudaMemcpyHostToDevice, st), "scaling");
+  }
+  // ---------------- plan B: orthonormal basis, Rayleigh-Ritz, eigenpairs of K
+  Plan& B = h->p_fb;
+  B.clear();
+  {
+    std::vector<GemmDesc> gV, gQ, gA1, gA2, gR1, gR2, gR3, gR4;
+    std::vector<LuDesc> lu;
+    std::vector<EigDesc> eg;
+    for (auto& f : fp) {
+      PW& w = *f.w;
+      const int s = f.s, m0 = f.m0, k = f.k, q = f.q;
+      z64 *D = w.D[q], *U = w.a[q][0], *L = w.b[q][0];
+      // Vs = GZ * PS (m0 x k), Qt = Q Vs (2s x k): orthonormal basis of span Q
+      gV.push_back(gdesc(m0, k, m0, plain(f.GZ, m0), plain(f.PS, m0), f.GX, k, ONE, ZERO));
+      gQ.push_back(gdesc(2 * s, k, m0, plain(f.Q, m0), plain(f.GX, k), f.Qt, k, ONE, ZERO));
+      const z64* Qt1 = f.Qt;
+      const z64* Qt2 = f.Qt + (size_t)s * k;
+      // A Qt = [Qt2; -L Qt1 - D Qt2], B Qt = [Qt1; U Qt2]
+      z64* AQ2 = f.AQ;
+      z64* BQ2 = f.AQ + (size_t)s * k;
+      gA1.push_back(gdesc(s, k, s, plain(L, s), plain(Qt1, k), AQ2, k, MONE, ZERO));
+      gA2.push_back(gdesc(s, k, s, plain(D, s), plain(Qt2, k), AQ2, k, MONE, ONE));
+      gA1.push_back(gdesc(s, k, s, plain(U, s), plain(Qt2, k), BQ2, k, ONE, ZERO));
+      // RR = [Qt^H B Qt | Qt^H A Qt] (k x 2k)
+      z64* Bh = f.RR;
+      z64* Ah = f.RR + k;
+      gR1.push_back(gdesc(k, k, s, plain(Qt1, k, 1), plain(Qt1, k), Bh, 2 * k, ONE, ZERO));
+      gR2.push_back(gdesc(k, k, s, plain(Qt2, k, 1), plain(BQ2, k), Bh, 2 * k, ONE, ONE));
+      gR3.push_back(gdesc(k, k, s, plain(Qt1, k, 1), plain(Qt2, k), Ah, 2 * k, ONE, ZERO));
+      gR4.push_back(gdesc(k, k, s, plain(Qt2, k, 1), plain(AQ2, k), Ah, 2 * k, ONE, ONE));
+      LuDesc Ld{};
+      Ld.w = f.RR; Ld.ldw = 2 * k; Ld.s = k; Ld.ncols = 2 * k; Ld.ipiv = f.piv; Ld.info = f.info + 2;
+      lu.push_back(Ld);
+    }
+    B.gemm(gV);
+    B.gemm(gQ);
+    B.gemm(gA1);
+    B.gemm(gA2);
+    B.gemm(gR1);
+    B.gemm(gR2);
+    B.gemm(gR3);
+    B.gemm(gR4);
+    ::lu(h, B, lu);
+    // K = B^-1 A sits in the right half of RR: copy it out (ld k) for the eigen-solver
+    std::vector<FormDesc> fk;
+    for (auto& f : fp) {
+      fk.push_back(fcopy(f.KZ, f.k, f.RR + f.k, 2 * f.k, f.k, f.k));
+      eg.push_back({f.KZ, f.KX, f.ZX, f.Klam, f.k, f.k, f.info + 3});
+    }
+    B.form(fk);
+    B.eig(eg);
+    // eigenvectors of K: (Z X); modes u = first half of Qt (Z X)
+    std::vector<GemmDesc> gY, gU;
+    for (auto& f : fp) {
+      const int s = f.s, k = f.k;
+      gY.push_back(gdesc(k, k, k, plain(f.KX, k), plain(f.ZX, k), f.GX, k, ONE, ZERO));
+      gU.push_back(gdesc(s, k, k, plain(f.Qt, k), plain(f.GX, k), f.Ua, k, ONE, ZERO));
+    }
+    B.gemm(gY);
+    B.gemm(gU);
+  }
+  CK(B.upload(st), "upload feast B");
+  CK(B.run(st, &h->nlaunch, h->P()), "feast Rayleigh-Ritz");
+  std::vector<std::vector<z64>> lam(fp.size());
+  for (size_t i = 0; i < fp.size(); ++i) {
+    lam[i].resize(fp[i].k);
+    CK(cudaMemcpyAsync(lam[i].data(), fp[i].Klam, sizeof(z64) * fp[i].k, cudaMemcpyDeviceToHost, st), "ritz values");
+  }
+  CK(cudaMemcpyAsync(finfo.data(), h->feast_info, sizeof(int) * finfo.size(), cudaMemcpyDeviceToHost, st), "info");
+  CK(cudaStreamSynchronize(st), "feast sync");
+  // ---------------- host: modes inside the annulus moving towards the bulk
+  for (size_t i = 0; i < fp.size(); ++i) {
+    FeastProb& f = fp[i];
+    if (finfo[i * 8 + 2] || finfo[i * 8 + 3])
+      return fail(h, SS_ERR_SINGULAR, "contour-integral Rayleigh-Ritz failed (singular B^ or eigen-iteration cap)");
+    std::vector<z64> S((size_t)f.k * f.s, ZERO), Sf((size_t)f.k * f.s, ZERO);
+    int m = 0;
+    for (int j = 0; j < f.k && m < f.s; ++j) {
+      const double a = std::hypot(lam[i][j].x, lam[i][j].y);
+      if (!(a > 1.0 / Rr && a < Rr)) continue;
+      if (f.q == 1 ? !(a < 1.0) : !(a > 1.0)) continue;
+      const z64 l = lam[i][j];
+      const z64 fv = f.q == 1 ? l : zinv_host(l);
+      S[(size_t)j * f.s + m] = ONE;  // column m of U_m = column j of Ua (k x s selection, ld s)
+      Sf[(size_t)j * f.s + m] = fv;
+      ++m;
+    }
+    f.mm = m;
+    if (m == 0) return fail(h, SS_ERR_SINGULAR, "no lead mode found inside the annulus");
+    CK(cudaMemcpyAsync(f.PS, S.data(), S.size() * sizeof(z64), cudaMemcpyHostToDevice, st), "selection");
+    CK(cudaMemcpyAsync(f.PF, Sf.data(), Sf.size() * sizeof(z64), cudaMemcpyHostToDevice, st), "selection");
+  }
+  // ---------------- plan C: F, surface Green's function, self-energy
+  Plan& C = h->p_fc;
+  C.clear();
+  {
+    std::vector<GemmDesc> gS, gG1, gF, gE, gSig;
+    std::vector<FormDesc> fU, fE, fT, fS;
+    std::vector<LuDesc> lu1, lu2;
+    for (auto& f : fp) {
+      PW& w = *f.w;
+      const int s = f.s, k = f.k, m = f.mm, q = f.q;
+      z64 *D = w.D[q], *U = w.a[q][0], *L = w.b[q][0];
+      // Ut = Ua Psel (s x m), Uf = Ua Pf (s x m)
+      gS.push_back(gdesc(s, m, k, plain(f.Ua, k), plain(f.PS, s), f.Ut, m, ONE, ZERO));
+      gS.push_back(gdesc(s, m, k, plain(f.Ua, k), plain(f.PF, s), f.Uf, m, ONE, ZERO));
+      // GG = [Ut^H Ut | Ut^H] (m x (m + s)) -> (Ut^H Ut)^-1 Ut^H, or for m = s [Ut^H | Uf^H] -> Ut^-H Uf^H = F^H
+      if (m == s) {
+        fU.push_back(fcopy(f.GG, 2 * s, f.Ut, s, s, s, 1));
+        fU.push_back(fcopy(f.GG + s, 2 * s, f.Uf, s, s, s, 1));
+        LuDesc Ld{};
+        Ld.w = f.GG; Ld.ldw = 2 * s; Ld.s = s; Ld.ncols = 2 * s; Ld.ipiv = f.piv; Ld.info = f.info + 4;
+        lu1.push_back(Ld);
+        fT.push_back(fcopy(f.F, s, f.GG + s, 2 * s, s, s, 1));  // F = (F^H)^H
+      } else {
+        gG1.push_back(gdesc(m, m, s, plain(f.Ut, m, 1), plain(f.Ut, m), f.GG, m + s, ONE, ZERO));
+        fU.push_back(fcopy(f.GG + m, m + s, f.Ut, m, m, s, 1));
+        LuDesc Ld{};
+        Ld.w = f.GG; Ld.ldw = m + s; Ld.s = m; Ld.ncols = m + s; Ld.ipiv = f.piv; Ld.info = f.info + 4;
+        lu1.push_back(Ld);
+        gF.push_back(gdesc(s, s, m, plain(f.Uf, m), plain(f.GG + m, m + s), f.F, s, ONE, ZERO));
+      }
+      // es = D + U F (right) / D + L F (left) into Wd = [es | A]
+      const z64 E = make_double2(w.E, 0.0);
+      const z64* const* cc = w.kd->cell[q];
+      z64* W = w.Wd[q];
+      const int ld = 3 * s;
+      fE.push_back(fcopy(W, ld, D, s, s, s));
+      gE.push_back(gdesc(s, s, s, plain(q == 1 ? U : L, s), plain(f.F, s), W, ld, ONE, ONE));
+      // right: rhs A_{n+1,n} = (E S01 - H01)^H ; left: rhs A_{0,1} = E S01 - H01
+      fS.push_back(fformed(W + s, ld, cc[3], cc[1], E, s, s, s, q == 1 ? 1 : 0));
+      LuDesc L2{};
+      L2.w = W; L2.ldw = ld; L2.s = s; L2.ncols = 2 * s; L2.ipiv = w.ipd[q]; L2.info = f.info + 5;
+      lu2.push_back(L2);
+      gSig.push_back(gdesc(s, s, s, formed(cc[3], cc[1], E, s, q == 1 ? 0 : 1), plain(W + s, ld), w.sig[q], s, ONE, ZERO));
+    }
+    C.gemm(gS);
+    C.gemm(gG1);
+    C.form(fU);
+    ::lu(h, C, lu1);
+    C.gemm(gF);
+    C.form(fT);
+    C.form(fE);
+    C.gemm(gE);
+    C.form(fS);
+    ::lu(h, C, lu2);
+    C.gemm(gSig);
+  }
+  if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the contour solver");
+  CK(C.upload(st), "upload feast C");
+  CK(C.run(st, &h->nlaunch, h->P()), "feast self-energy");
+  CK(cudaMemcpyAsync(finfo.data(), h->feast_info, sizeof(int) * finfo.size(), cudaMemcpyDeviceToHost, st), "info");
+  CK(cudaStreamSynchronize(st), "feast sync");
+  for (size_t i = 0; i < fp.size(); ++i)
+    if (finfo[i * 8 + 4] || finfo[i * 8 + 5]) return fail(h, SS_ERR_SINGULAR, "singular mode matrix or surface block");
+  return SS_OK;
+}
+
 bool same_points(const ss_handle* h, int n, const double* E, const int* k) {
   if ((int)h->cE.size() != n) return false;
   for (int i = 0; i < n; ++i)
@@ -1318,6 +1741,11 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     std::vector<int> seeded;  // 2 per point: lead seeded by an accepted warm start
     if (!reuse_sigma) {
       h->plan_error = false;
+      if (h->cfg.obc == SS_OBC_FEAST) {
+        // the leads' Bloch modes by the contour integral, then Sigma from them
+        const int r = run_feast(h, pts);
+        if (r) return r;
+      } else {
       if (h->cfg.warm_start) {
         // learned warm start of each lead that has a network attached (points
         // of the network's block size); rejected seeds fall back to the doubling
@@ -1351,7 +1779,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       CK(h->p_iter[0].upload(st), "upload iter");
       CK(h->p_iter[1].upload(st), "upload iter");
       CK(h->p_final.upload(st), "upload final");
-      CK(h->p_setup.run(st, &h->nlaunch, h->P()), "decimation setup");
+      CK(h->p_setup.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "decimation setup");
       std::vector<int> h_act(2 * P, 1);
       const int cap = h->cfg.decim_max_iter;
       if (h->cfg.profile) {
@@ -1387,13 +1815,15 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
           if (!any) break;
         }
       }
-      CK(h->p_final.run(st, &h->nlaunch, h->P()), "self-energy");
+      CK(h->p_final.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "self-energy");
       CK(cudaMemcpyAsync(h_it.data(), itr, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read iters");
       CK(cudaMemcpyAsync(h_conv.data(), conv, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, st), "read conv");
       CK(cudaMemcpyAsync(h_dinfo.data(), dinfo, sizeof(int) * 4 * P, cudaMemcpyDeviceToHost, st), "read info");
       CK(cudaStreamSynchronize(st), "self-energy sync");
       for (int i = 0; i < (int)seeded.size(); ++i)
         if (seeded[i]) { h_conv[i] = 1; h_it[i] = -WARM_ITERS; }  // accepted seed: converged, steps as negative count
+      }
+
     } else {
       for (int p = 0; p < P; ++p) {
         h_it[2 * p] = h->c_iters[2 * pts[p].idx];
@@ -1420,8 +1850,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the sweeps");
       CK(h->p_sweep.upload(st), "upload sweeps");
       CK(h->p_bound.upload(st), "upload diagonal blocks");
-      CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
-      CK(h->p_bound.run(st, &h->nlaunch, h->P()), "diagonal blocks");
+      CK(h->p_sweep.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "sweeps");
+      CK(h->p_bound.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "diagonal blocks");
       launch_scaled_imag(h->dtr, dosv, P * nmax, -1.0 / M_PI, st);
       ++h->nlaunch;
       CK(cudaGetLastError(), "density of states");
@@ -1442,8 +1872,8 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       if (h->plan_error) return fail(h, SS_ERR_OOM, "tensor-core packing buffer too small for the sweeps");
       CK(h->p_sweep.upload(st), "upload sweeps");
       CK(h->p_bound.upload(st), "upload boundary");
-      CK(h->p_sweep.run(st, &h->nlaunch, h->P()), "sweeps");
-      CK(h->p_bound.run(st, &h->nlaunch, h->P()), "boundary");
+      CK(h->p_sweep.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "sweeps");
+      CK(h->p_bound.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "boundary");
       if (refine) {
         // FP64 iterative refinement of x until the normwise backward error
         // ||r|| / (||A - Sigma|| ||x|| + ||Inj||) (Frobenius norms) is <= ir_tol
@@ -1461,7 +1891,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
         CK(cudaMemcpyAsync(hm.data(), mm, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
         double prev = HUGE_VAL;
         for (int it = 0;; ++it) {
-          CK(h->p_ir_res.run(st, &h->nlaunch, h->P()), "residual");
+          CK(h->p_ir_res.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "residual");
           CK(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
           CK(cudaMemcpyAsync(hx.data(), xx, sizeof(double) * P, cudaMemcpyDeviceToHost, st), "read");
           CK(cudaStreamSynchronize(st), "refinement sync");
@@ -1476,7 +1906,7 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
           // halves the residual (FP64 working accuracy: more steps cannot help)
           if (worst_rel <= h->cfg.ir_tol || it >= h->cfg.ir_max_iter || worst_rel > 0.5 * prev) break;
           prev = worst_rel;
-          CK(h->p_ir_cor.run(st, &h->nlaunch, h->P()), "correction");
+          CK(h->p_ir_cor.execute(st, &h->nlaunch, h->P(), h->cfg.use_graphs), "correction");
         }
       }
       h_sinfo.assign(n_sinfo, 0);
@@ -1606,6 +2036,11 @@ void ss_config_default(ss_config* cfg) {
   cfg->profile = 0;
   cfg->partitions = 1;
   cfg->memory_lean = 0;
+  cfg->hermitian_sweeps = 0;
+  cfg->obc = SS_OBC_DECIMATION;
+  cfg->feast_radius = 50.0;
+  cfg->feast_points = 16;
+  cfg->feast_subspace = 0;
 }
 
 int ss_create(ss_handle** hp, const ss_config* cfg) {
@@ -1625,6 +2060,16 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
   }
   if (!(cfg->eta >= 0.0) || !(cfg->decim_tol >= 0.0) || cfg->decim_max_iter < 1) {
     g_create_error = "invalid eta / decim_tol / decim_max_iter";
+    return SS_ERR_ARG;
+  }
+  if (cfg->obc != SS_OBC_DECIMATION && cfg->obc != SS_OBC_FEAST) {
+    g_create_error = "obc must be SS_OBC_DECIMATION or SS_OBC_FEAST";
+    return SS_ERR_ARG;
+  }
+  if (cfg->obc == SS_OBC_FEAST &&
+      (!(cfg->feast_radius > 1.0) || cfg->feast_points < 2 || cfg->feast_subspace < 0 ||
+       2 * cfg->s_b_max > 512 + (cfg->feast_subspace > 0 ? 1 << 30 : 0) || cfg->feast_subspace > 512)) {
+    g_create_error = "contour solver: radius > 1, points >= 2, subspace 0..512 (0: 2 s_b, needs s_b <= 256)";
     return SS_ERR_ARG;
   }
   if (cfg->partitions < 1 || cfg->partitions > MAXP) {
@@ -1751,9 +2196,18 @@ int ss_set_hamiltonian(ss_handle* h, int k_id, int n_b, int s_b, const ss_c64* H
   return SS_OK;
 }
 
+// Counts the host-side launch calls of one public call into h->nhost.
+struct HostCalls {
+  ss_handle* h;
+  long long c0;
+  explicit HostCalls(ss_handle* hh) : h(hh), c0(host_launch_calls()) {}
+  ~HostCalls() { if (h) h->nhost += host_launch_calls() - c0; }
+};
+
 int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id, ss_c64* sigma_L, ss_c64* sigma_R,
                    int* iters, int* status) {
   if (!h) return SS_ERR_ARG;
+  HostCalls hc(h);
   h->err.clear();
   Want w;
   w.sigma_out = true;
@@ -1774,6 +2228,7 @@ int ss_self_energy(ss_handle* h, int n_pts, const double* E, const int* k_id, ss
 int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id, int n_inj, const ss_c64* inj, ss_c64* x,
              int* status) {
   if (!h) return SS_ERR_ARG;
+  HostCalls hc(h);
   h->err.clear();
   if (n_inj < 1 || n_inj > h->cfg.max_inj) return fail(h, SS_ERR_ARG, "n_inj outside 1..max_inj");
   if (!inj) return fail(h, SS_ERR_ARG, "NULL injection");
@@ -1792,6 +2247,7 @@ int ss_solve(ss_handle* h, int n_pts, const double* E, const int* k_id, int n_in
 int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, double* T, double* err_est,
                     int* status) {
   if (!h) return SS_ERR_ARG;
+  HostCalls hc(h);
   h->err.clear();
   if (!T && n_pts > 0) return fail(h, SS_ERR_ARG, "NULL T");
   std::vector<double> Tv, Ti;
@@ -1829,6 +2285,7 @@ int ss_transmission(ss_handle* h, int n_pts, const double* E, const int* k_id, d
 
 int ss_dos(ss_handle* h, int n_pts, const double* E, const int* k_id, double* dos, int* status) {
   if (!h) return SS_ERR_ARG;
+  HostCalls hc(h);
   h->err.clear();
   if (!dos && n_pts > 0) return fail(h, SS_ERR_ARG, "NULL dos");
   Want w;
@@ -2116,6 +2573,9 @@ int ss_destroy(ss_handle* h) {
   cudaFree(h->feat);
   cudaFree(h->warm_y);
   cudaFree(h->wres);
+  cudaFree(h->feast_buf);
+  cudaFree(h->feast_info);
+  h->p_fa.clear(); h->p_fb.clear(); h->p_fc.clear();
   h->p_warm_iter.clear(); h->p_warm_judge.clear(); h->p_final_g.clear();
   h->p_ir_res.clear(); h->p_ir_cor.clear();
   h->p_setup.clear(); h->p_iter[0].clear(); h->p_iter[1].clear();
@@ -2132,6 +2592,8 @@ const char* ss_last_error(const ss_handle* h) {
 }
 
 long long ss_launch_count(const ss_handle* h) { return h ? h->nlaunch : 0; }
+
+long long ss_host_launch_count(const ss_handle* h) { return h ? h->nhost : 0; }
 
 int ss_exact_gemm_plan(int k, int* w, int* beta, int* S, int* npass, unsigned char* pd, unsigned char* pt0,
                        unsigned char* pnp) {

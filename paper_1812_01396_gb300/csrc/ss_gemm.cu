@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(const GemmDesc* __restrict__ 
   const int tiles_n = (n + TN - 1) / TN;
   const int t = blockIdx.x - __ldg(tile_start + pid);
   const int row0 = (t / tiles_n) * TM, col0 = (t % tiles_n) * TN;
+  if (d.lower && col0 >= row0 + TM) return;  // tile entirely above the diagonal
   const Operand a = d.a, b = d.b;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
 

@@ -64,6 +64,7 @@ struct GemmDesc {
   z64 ce;
   int ldcf;
   const int* active;
+  int lower;  // 1: only the lower triangle of C (m = n) is needed; tiles above the diagonal are skipped
 };
 
 // Elementwise out = ax*op(X) + ay*op(Y) + az*op(Z) + gamma*I over rows x cols.
@@ -92,6 +93,20 @@ struct LuDesc {
   int* info;     // 0, or 1 + first column with a zero / non-finite pivot
   const int* active;
 };
+
+// Dense complex eigenproblem K y = lambda y of size m <= 512 (ss_eig.cu):
+// h holds K on entry and its Schur form T on exit, z receives the unitary
+// Z with K = Z T Z^H, x the eigenvectors of T (column j for lam[j]; the
+// eigenvectors of K are Z x), all m x m with leading dimension ld.
+struct EigDesc {
+  z64* h;
+  z64* z;
+  z64* x;
+  z64* lam;
+  int m, ld;
+  int* info;  // 1 if the QR iteration hit its cap
+};
+void launch_eig(const EigDesc* d, int nprob, cudaStream_t st);
 
 // Norm / reduction descriptors
 struct Norm1Desc {
@@ -133,6 +148,8 @@ void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int
                         cudaStream_t st);
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs,
                             cudaStream_t st);
+// Hermitian LDL^H panel without pivoting (see ss_lu.cu); smax: largest block of the group.
+void launch_herm_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st);
 
 void launch_norm1(const Norm1Desc* d, int nprob, int max_cols, cudaStream_t st);
 void launch_trace(const TraceDesc* d, int nprob, cudaStream_t st);

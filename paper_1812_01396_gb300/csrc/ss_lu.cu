@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
   const int s = d.s;
   if (k0 >= s) return;
   const int nbw = min(min(nb, NB), s - k0);
-  const int K1 = nbo > 0 ? min((k0 / nbo) * nbo + nbo, s) : d.ncols;
+  // nbo < 0 (Hermitian factorisation): only the right-hand-side columns, from s on
+  const int K1 = nbo > 0 ? min((k0 / nbo) * nbo + nbo, s) : (nbo < 0 ? s : d.ncols);
   __shared__ z64 Ls[NB][NB + 1];
   __shared__ int piv[NB];
   for (int e = threadIdx.x; e < nbw * nbw; e += RB_THREADS) {
@@ -557,7 +558,127 @@ __global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDes
   for (int j = 0; j < NB; ++j)
     if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
 }
+// Hermitian LDL^H panel without pivoting (the factorisation of the sweep
+// blocks D_i, which are Hermitian at real E; the paper factors them with a
+// no-pivoting Hermitian solver, Sec. 5E).  Only the lower triangle of the
+// trailing matrix is kept up to date.  Two launches per panel:
+//   herm_diag  one CTA per problem reads the lower triangle of the nb x nb
+//              diagonal block, factors it as L11 D1 L11^H in shared memory and
+//              writes L11 (strictly lower), D1 (diagonal) and U11 = D1 L11^H
+//              (upper) back;
+//   herm_rows  CTA x solves its HP_THREADS rows of A21 against U11,
+//              L21 = A21 U11^-1, and writes U12 = D1 L21^H (the transposed rows)
+//              into the upper triangle.
+// The result has the layout of the LU code (unit L below the diagonal, U on
+// and above it, no row exchanges), so its right-hand-side solve, trailing
+// update (restricted to the lower triangle) and back substitution apply
+// unchanged.  A zero or non-finite d_j records 1 + its column in *info.
+constexpr int HP_THREADS = 128;
+
+template <int NB>
+__global__ void __launch_bounds__(HP_THREADS) herm_diag_kernel(const LuDesc* __restrict__ descs, int k0, int nb) {
+  const LuDesc d = descs[blockIdx.x];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(min(nb, NB), s - k0);
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  __shared__ z64 Dg[NB][NB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < nbw * nbw; e += HP_THREADS) {
+    const int i = e / nbw, j = e % nbw;
+    if (j <= i) Dg[i][j] = w[(size_t)(k0 + i) * ld + k0 + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < nbw; ++j) {
+    const z64 dj = Dg[j][j];
+    const z64 inv = zinv(dj);  // zero for a zero pivot (recorded below)
+    const int m = nbw - 1 - j;
+    // Dg[i][c] -= Dg[i][j] conj(Dg[c][j]) / d_j for j < c <= i (column j still unscaled)
+    for (int e = tid; e < m * m; e += HP_THREADS) {
+      const int i = j + 1 + e / m, c = j + 1 + e % m;
+      if (c <= i) Dg[i][c] = zsub(Dg[i][c], zmul(zmul(Dg[i][j], inv), zconj(Dg[c][j])));
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nbw; i += HP_THREADS) Dg[i][j] = zmul(Dg[i][j], inv);
+    if (tid == 0) {
+      const double a = fabs(dj.x) + fabs(dj.y);
+      if (bad == 0 && !(a > 0.0 && a <= 1.7976931348623157e308)) bad = j + 1;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nbw * nbw; e += HP_THREADS) {
+    const int i = e / nbw, j = e % nbw;
+    w[(size_t)(k0 + i) * ld + k0 + j] = j <= i ? Dg[i][j] : zmul(Dg[i][i], zconj(Dg[j][i]));
+  }
+  for (int t = tid; t < nbw; t += HP_THREADS) d.ipiv[k0 + t] = k0 + t;
+  if (tid == 0 && bad && d.info && *d.info == 0) *d.info = k0 + bad;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(HP_THREADS) herm_rows_kernel(const LuDesc* __restrict__ descs, int k0, int nb) {
+  const LuDesc d = descs[blockIdx.y];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (k0 >= s) return;
+  const int nbw = min(min(nb, NB), s - k0);
+  const int r = k0 + nbw + blockIdx.x * HP_THREADS + threadIdx.x;
+  if (k0 + nbw + blockIdx.x * HP_THREADS >= s) return;  // no rows for this CTA (uniform)
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  __shared__ z64 Uu[NB][NB + 1];  // U11 = D1 L11^H, upper triangle with the diagonal
+  __shared__ z64 dinv[NB];
+  for (int e = threadIdx.x; e < nbw * nbw; e += HP_THREADS) {
+    const int c = e / nbw, j = e % nbw;
+    if (c <= j) Uu[c][j] = w[(size_t)(k0 + c) * ld + k0 + j];
+  }
+  __syncthreads();
+  if (threadIdx.x < nbw) dinv[threadIdx.x] = zinv(Uu[threadIdx.x][threadIdx.x]);
+  __syncthreads();
+  if (r >= s) return;
+  z64 a[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) a[c] = c < nbw ? w[(size_t)r * ld + k0 + c] : zmk(0.0, 0.0);
+  // l U11 = a: l_j = (a_j - sum_{c<j} l_c U_cj) / d_j
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < nbw) {
+      z64 acc = a[j];
+#pragma unroll
+      for (int c = 0; c < j; ++c) {
+        const z64 u = Uu[c][j];
+        acc.x = fma(-a[c].x, u.x, acc.x);
+        acc.x = fma(a[c].y, u.y, acc.x);
+        acc.y = fma(-a[c].x, u.y, acc.y);
+        acc.y = fma(-a[c].y, u.x, acc.y);
+      }
+      a[j] = zmul(acc, dinv[j]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    if (c < nbw) {
+      w[(size_t)r * ld + k0 + c] = a[c];
+      w[(size_t)(k0 + c) * ld + r] = zmul(Uu[c][c], zconj(a[c]));  // U12 = D1 L21^H
+    }
+}
 }  // namespace
+
+void launch_herm_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st) {
+  if (nprob <= 0 || k0 >= smax) return;
+  const int rows = smax - k0 - nb;
+  dim3 grid(rows > 0 ? (rows + HP_THREADS - 1) / HP_THREADS : 1, nprob);
+  if (nb <= 16) {
+    herm_diag_kernel<16><<<nprob, HP_THREADS, 0, st>>>(d, k0, nb);
+    if (rows > 0) herm_rows_kernel<16><<<grid, HP_THREADS, 0, st>>>(d, k0, nb);
+  } else {
+    herm_diag_kernel<MAXNB><<<nprob, HP_THREADS, 0, st>>>(d, k0, nb);
+    if (rows > 0) herm_rows_kernel<MAXNB><<<grid, HP_THREADS, 0, st>>>(d, k0, nb);
+  }
+}
 
 int lu_panel_width(int smax) {
   if (smax <= 512) return 16;

@@ -94,6 +94,7 @@ __device__ __forceinline__ bool oz_tile(const OzDesc* __restrict__ descs, const 
   const int gm = min(GM, tiles_m - first), r = t - group * GM * tiles_n;
   m0 = (first + r % gm) * BM;
   n0 = (r / gm) * BN;
+  if (d.lower && (n0 >> 1) >= m0 + BM) return false;  // tile entirely above the diagonal
   return true;
 }
 

@@ -8,6 +8,11 @@
 namespace ss {
 
 namespace {
+thread_local long long g_host_calls = 0;
+}  // namespace
+long long host_launch_calls() { return g_host_calls; }
+
+namespace {
 struct OpKey {
   const void* p; const void* s; double er, ei; int ld, trans, rows, k, role;
   bool operator<(const OpKey& o) const {
@@ -147,7 +152,7 @@ bool Plan::oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, s
     t.mA = pk[amap[i]].maxb;
     t.mB = pk[bmap[i]].maxb;
     t.c = g.c; t.ldc = g.ldc; t.cmode = g.cmode; t.alpha = g.alpha; t.beta = g.beta;
-    t.cs = g.cs; t.ch = g.ch; t.ce = g.ce; t.ldcf = g.ldcf; t.active = g.active;
+    t.cs = g.cs; t.ch = g.ch; t.ce = g.ce; t.ldcf = g.ldcf; t.active = g.active; t.lower = g.lower;
     ods[i] = t;
     start[i] = tot;
     tot += oz_tiles(t.m, t.n2);
@@ -415,6 +420,73 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   return ok;
 }
 
+bool Plan::ldl_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err) {
+  if (ds.empty()) return true;
+  bool ok = true;
+  auto update = [&](const std::vector<GemmDesc>& g) {
+    if (upd == UPD_EXACT_TC || upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
+    else gemm(g, true);
+  };
+  const int np = (int)ds.size();
+  int smax = 0, maxrhs = 0;
+  for (auto& d : ds) { smax = std::max(smax, d.s); maxrhs = std::max(maxrhs, d.ncols - d.s); }
+  if (nb <= 0) nb = 16;
+  nb = std::min(nb, 32);
+  const size_t off = push_vec(ds);
+  auto udesc = [](const LuDesc& d, int m, int n, int k, int ar, int ac, int br, int bc, int cr, int cc) {
+    GemmDesc q{};
+    q.m = m; q.n = n; q.k = k;
+    q.a.p = d.w + (size_t)ar * d.ldw + ac; q.a.ld = d.ldw;
+    q.b.p = d.w + (size_t)br * d.ldw + bc; q.b.ld = d.ldw;
+    q.c = d.w + (size_t)cr * d.ldw + cc; q.ldc = d.ldw;
+    q.alpha = make_double2(-1.0, 0.0); q.beta = make_double2(1.0, 0.0);
+    q.active = d.active;
+    return q;
+  };
+  for (int k0 = 0; k0 < smax; k0 += nb) {
+    LaunchRec r;
+    r.kind = K_LU_HPANEL;
+    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = smax;
+    recs_.push_back(r);
+    if (maxrhs > 0) {  // B1 = L11^-1 B1 on the right-hand sides (no row exchanges)
+      LaunchRec rr;
+      rr.kind = K_LU_ROW;
+      rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.nbo = -1; rr.ival = 1; rr.maxc = maxrhs;
+      recs_.push_back(rr);
+    }
+    std::vector<GemmDesc> g;
+    for (auto& d : ds) {
+      if (k0 >= d.s) continue;
+      const int nbw = std::min(nb, d.s - k0);
+      const int m = d.s - k0 - nbw;
+      if (m <= 0) continue;
+      GemmDesc q = udesc(d, m, m, nbw, k0 + nbw, k0, k0, k0 + nbw, k0 + nbw, k0 + nbw);
+      q.lower = 1;  // A22 -= L21 U12 on the lower triangle
+      g.push_back(q);
+      if (d.ncols > d.s) g.push_back(udesc(d, m, d.ncols - d.s, nbw, k0 + nbw, k0, k0, d.s, k0 + nbw, d.s));
+    }
+    update(g);
+  }
+  if (maxrhs <= 0) return ok;
+  // back substitution with U = D L^H (written by the panels), as in lu_solve
+  const int last = ((smax - 1) / nb) * nb;
+  for (int k0 = last; k0 >= 0; k0 -= nb) {
+    LaunchRec r;
+    r.kind = K_LU_BACK;
+    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = maxrhs;
+    recs_.push_back(r);
+    if (k0 == 0) break;
+    std::vector<GemmDesc> g;
+    for (auto& d : ds) {
+      if (k0 >= d.s || d.ncols <= d.s) continue;
+      const int nbw = std::min(nb, d.s - k0);
+      g.push_back(udesc(d, k0, d.ncols - d.s, nbw, 0, k0, k0, d.s, 0, d.s));
+    }
+    update(g);
+  }
+  return ok;
+}
+
 void Plan::destroy_graph() {
   if (exec_) cudaGraphExecDestroy(exec_);
   exec_ = nullptr;
@@ -428,10 +500,29 @@ void Plan::release() {
   devcap_ = 0;
 }
 
+// Hash of everything a captured launch depends on except the descriptor
+// contents: the device buffer, and per launch its kind, grid sizes, offsets
+// into the buffer, scalar and pointer arguments.
+size_t Plan::signature() const {
+  size_t h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ull; };
+  mix((unsigned long long)(uintptr_t)dev_);
+  mix(recs_.size());
+  for (const LaunchRec& r : recs_) {
+    mix((unsigned long long)r.kind); mix(r.off); mix(r.toff); mix((unsigned)r.nprob); mix((unsigned)r.tiles);
+    mix((unsigned)r.k0); mix((unsigned)r.nb); mix((unsigned)r.maxc); mix((unsigned)r.nbo);
+    unsigned long long tb;
+    std::memcpy(&tb, &r.tol, sizeof(tb));
+    mix(tb); mix((unsigned)r.cap); mix((unsigned)r.count); mix((unsigned)r.ival); mix(r.bytes);
+    for (int i = 0; i < 6; ++i) mix((unsigned long long)(uintptr_t)r.p[i]);
+  }
+  return h;
+}
+
 cudaError_t Plan::upload(cudaStream_t st) {
-  destroy_graph();
   const size_t need = host_.size() ? host_.size() : 16;
   if (need > devcap_) {
+    destroy_graph();
     if (dev_) {
       cudaError_t e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return e;
@@ -443,6 +534,11 @@ cudaError_t Plan::upload(cudaStream_t st) {
     if (e != cudaSuccess) { dev_ = nullptr; devcap_ = 0; return e; }
     devcap_ = cap;
   }
+  const size_t sig = signature();
+  repeat_ = sig == last_sig_;
+  last_sig_ = sig;
+  runs_ = 0;
+  if (exec_ && sig != graph_sig_) destroy_graph();
   if (host_.empty()) return cudaSuccess;
   return cudaMemcpyAsync(dev_, host_.data(), host_.size(), cudaMemcpyHostToDevice, st);
 }
@@ -470,11 +566,13 @@ static double gemm_flops(const LaunchRec& r, const std::vector<unsigned char>& h
   if (r.kind == K_GEMM || r.kind == K_GEMM32 || r.kind == K_GEMM_LU) {
     const GemmDesc* g = reinterpret_cast<const GemmDesc*>(host.data() + r.off);
     for (int i = 0; i < r.nprob; ++i)
-      if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)g[i].n * g[i].k;
+      if (prof_active(g[i].active, prof))
+        f += 8.0 * g[i].k * (g[i].lower ? 0.5 * g[i].m * (double)(g[i].n + 1) : g[i].m * (double)g[i].n);
   } else if (r.kind == K_OZGEMM || r.kind == K_OZGEMM_LU) {
     const OzDesc* g = reinterpret_cast<const OzDesc*>(host.data() + r.off);
     for (int i = 0; i < r.nprob; ++i)
-      if (prof_active(g[i].active, prof)) f += 8.0 * g[i].m * (double)(g[i].n2 / 2) * (double)g[i].kc;
+      if (prof_active(g[i].active, prof))
+        f += 8.0 * g[i].kc * (g[i].lower ? 0.5 * g[i].m * (double)(g[i].n2 / 2 + 1) : g[i].m * (double)(g[i].n2 / 2));
   } else if (r.kind == K_TCGEMM) {
     // algorithmic complex flops (8 m n k), not the split-term tensor flops
     const TcDesc* g = reinterpret_cast<const TcDesc*>(host.data() + r.off);
@@ -515,6 +613,10 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
       }
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
       case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
+      case K_LU_HPANEL:
+        launch_herm_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st);
+        n += (r.maxc - r.k0 - r.nb > 0) ? 2 : 1;
+        break;
       case K_LU_ROW:
         if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.nbo, r.ival, r.maxc, st); ++n; }
         break;
@@ -522,6 +624,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
       case K_FROB2: launch_frob2((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;
       case K_NORM1: launch_norm1((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;
       case K_TRACE: launch_trace((const TraceDesc*)d, r.nprob, st); ++n; break;
+      case K_EIG: launch_eig((const EigDesc*)d, r.nprob, st); ++n; break;
       case K_CHECK:
         launch_decim_check((double*)r.p[0], (double*)r.p[1], (const double*)r.p[2], (int*)r.p[3],
                            (int*)r.p[4], (int*)r.p[5], r.nprob, r.tol, r.cap, r.count, st);
@@ -547,6 +650,8 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
       prof->recs.push_back(pr);
     }
   }
+  g_host_calls += n + (long long)std::count_if(recs_.begin(), recs_.end(),
+                                                [](const LaunchRec& r) { return r.kind == K_MEMSET; });
   if (nlaunch) *nlaunch += n;
   return cudaGetLastError();
 }
@@ -565,8 +670,10 @@ cudaError_t Plan::replay(cudaStream_t st, long long* nlaunch) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { exec_ = nullptr; return e; }
     graph_kernels_ = n;
+    graph_sig_ = signature();
   }
   cudaError_t e = cudaGraphLaunch(exec_, st);
+  ++g_host_calls;
   if (nlaunch) *nlaunch += graph_kernels_;
   return e;
 }

@@ -13,10 +13,14 @@
 
 namespace ss {
 
+// Host-side launch calls made by this thread through plans: one per eager
+// kernel launch or memset, one per graph launch.
+long long host_launch_calls();
+
 // Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
 enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
                   K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_OZSCALE, K_OZPACK, K_OZGEMM, K_FROB2,
-                  K_GEMM_LU, K_OZGEMM_LU, K_MEMSET };
+                  K_GEMM_LU, K_OZGEMM_LU, K_LU_HPANEL, K_EIG, K_MEMSET };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -64,10 +68,13 @@ struct Prof {
 class Plan {
  public:
   ~Plan() { release(); }
+  // Forget the recorded launches.  A captured graph is kept: if the next
+  // recording has the same launch sequence (same kinds, grid sizes, offsets
+  // and pointer arguments) and fits the same device buffer, upload() keeps it
+  // and replay() launches it again with the new descriptor contents.
   void clear() {
     host_.clear();
     recs_.clear();
-    destroy_graph();
   }
   size_t push(const void* data, size_t bytes, size_t align = 16) {
     size_t off = (host_.size() + align - 1) & ~(align - 1);
@@ -135,6 +142,13 @@ class Plan {
   // inside an outer block are FP64 unless upd is UPD_EXACT_ALL.
   bool lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
                 size_t cap = 0, int* err = nullptr, int nbo = 0);
+  // Hermitian LDL^H without pivoting of the leading s x s block of every
+  // problem (only its lower triangle is read), then the solve of the
+  // right-hand-side columns s..ncols-1: panels of nb columns, trailing updates
+  // on the lower triangle only (half the factorisation work of lu_solve),
+  // back substitution as lu_solve.  upd: FP64 or exact tensor-core updates.
+  bool ldl_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
+                 size_t cap = 0, int* err = nullptr);
   void norm1(const std::vector<Norm1Desc>& ds) {
     if (ds.empty()) return;
     LaunchRec r;
@@ -151,6 +165,14 @@ class Plan {
     r.off = push_vec(ds);
     r.nprob = (int)ds.size();
     for (auto& d : ds) r.maxc = d.cols > r.maxc ? d.cols : r.maxc;
+    recs_.push_back(r);
+  }
+  void eig(const std::vector<EigDesc>& ds) {
+    if (ds.empty()) return;
+    LaunchRec r;
+    r.kind = K_EIG;
+    r.off = push_vec(ds);
+    r.nprob = (int)ds.size();
     recs_.push_back(r);
   }
   void trace(const std::vector<TraceDesc>& ds) {
@@ -186,6 +208,16 @@ class Plan {
   cudaError_t run(cudaStream_t st, long long* nlaunch, Prof* prof = nullptr);
   // Capture run() into a graph on first use, then replay it.
   cudaError_t replay(cudaStream_t st, long long* nlaunch);
+  // run() or replay(): with graphs allowed and no profiling, a plan whose
+  // launch sequence repeats the previous upload's (or has a graph already)
+  // is replayed from its graph, any other runs eagerly (a one-off structure
+  // is not worth an instantiation).
+  cudaError_t execute(cudaStream_t st, long long* nlaunch, Prof* prof, bool graphs) {
+    if (!graphs || prof) return run(st, nlaunch, prof);
+    if (exec_ || repeat_ || runs_ > 0) return replay(st, nlaunch);  // the second run of one upload too
+    ++runs_;
+    return run(st, nlaunch, nullptr);
+  }
   bool empty() const { return recs_.empty(); }
 
  private:
@@ -198,6 +230,11 @@ class Plan {
   size_t devcap_ = 0;
   cudaGraphExec_t exec_ = nullptr;
   long long graph_kernels_ = 0;
+  size_t graph_sig_ = 0;  // signature of the launch sequence the graph was captured from
+  size_t last_sig_ = 0;   // signature of the previous upload
+  bool repeat_ = false;   // this upload repeats the previous one's launch sequence
+  int runs_ = 0;          // eager runs since the last upload
+  size_t signature() const;
 };
 
 }  // namespace ss

@@ -79,6 +79,7 @@ struct OzDesc {
   z64 ce;
   int ldcf;
   const int* active;
+  int lower;  // skip tiles entirely above the diagonal (complex indices)
 };
 
 size_t oz_smem_bytes();

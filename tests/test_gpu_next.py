@@ -221,3 +221,87 @@ def test_dos_closed_forms_on_gpu(ss):
         inb = np.abs(E - eps) < 2 * abs(tw)
         expect = float(np.sum(1.0 / (np.pi * np.sqrt(4 * tw * tw - (E - eps[inb]) ** 2))))
         assert np.allclose(rho[p], expect, rtol=1e-7, atol=1e-9)
+
+
+# ------------------------------------------- Hermitian LDL^H of the sweep blocks
+@pytest.mark.parametrize("prec", [0, 3])
+@pytest.mark.parametrize("n_b,s_b", [(16, 32), (5, 70), (3, 130), (4, 256), (7, 1)])
+def test_hermitian_sweeps_match_oracle(ss, prec, n_b, s_b):
+    """The sweep blocks D_i factored as L D L^H without pivoting (the paper's
+    no-pivoting Hermitian solver), updates on the lower triangle only: x, T and
+    Sigma at the parity bar of the pivoted LU."""
+    dev = synth.make_device(n_b, s_b, seed=120 + s_b)[0]
+    Es = [0.3, -0.45]
+    inj = [synth.make_injection(s_b, 3, seed=130 + i)[0] for i in range(2)]
+    r = run_points(ss, [dev, dev], Es, inj, precision=prec, hermitian_sweeps=1)
+    assert np.all(np.asarray(r["st_T"]) == 0)
+    for p in range(2):
+        check_point(r, p, dev, Es[p], inj[p])
+
+
+def test_hermitian_sweeps_with_partitions_and_lean_mode(ss):
+    dev = synth.make_device(9, 48, seed=140, band=12, s_pert=0.02)[0]
+    Es = [0.1, -0.7]
+    inj = [synth.make_injection(48, 2, seed=141 + i)[0] for i in range(2)]
+    r = run_points(ss, [dev, dev], Es, inj, hermitian_sweeps=1, partitions=3)
+    for p in range(2):
+        check_point(r, p, dev, Es[p], inj[p])
+    T, st = transmission_only(ss, [dev, dev], Es, hermitian_sweeps=1, precision=3)
+    assert np.all(st == 0)
+    for p in range(2):
+        assert dense.rel_T_err(float(T[p]), float(r["T"][p])) < 1e-9
+
+
+def test_hermitian_sweeps_halve_the_factorisation_flops(ss):
+    """The profiled algorithmic flops of the LU updates: with L D L^H the
+    trailing update of the matrix part of each sweep block covers its lower
+    triangle only, m (m + 1) / 2 instead of m^2 entries per panel (m rows below
+    the panel), the right-hand sides and the back substitution unchanged."""
+    dev = synth.make_device(6, 128, seed=150)[0]
+    fl = {}
+    for herm in (0, 1):
+        h = ss.Handle(n_b_max=6, s_b_max=128, max_points=1, max_inj=1, profile=1, hermitian_sweeps=herm)
+        try:
+            h.set_device(0, dev)
+            h.self_energy([0.2], [0])   # self-energies first: the next call profiles the sweeps only
+            h.profile_reset()
+            h.transmission([0.2], [0])
+            fl[herm] = h.profile_read("zgemm_lu")[1]
+        finally:
+            h.close()
+    nb, s_b, n_b = 16, 128, 6
+    per_lu = sum(8.0 * nb * 0.5 * m * (m - 1) for m in (s_b - nb - k0 for k0 in range(0, s_b, nb)))
+    expected = 2 * n_b * per_lu   # both sweep directions, every block
+    assert abs((fl[0] - fl[1]) - expected) <= 1e-9 * fl[0], (fl, expected)
+
+
+# ------------------------------------------------ whole-pipeline graph replay
+@pytest.mark.parametrize("prec", [0, 3])
+def test_repeated_batches_replay_graphs_bit_identically(ss, prec):
+    """A second batch of the same shapes replays the sweep, boundary and
+    refinement plans from CUDA graphs: the results equal eager launches bit for
+    bit, and the host issues a few dozen launch calls instead of thousands."""
+    dev = synth.make_device(6, 64, seed=160)[0]
+    inj = [synth.make_injection(64, 2, seed=161 + i)[0] for i in range(2)]
+    batches = [[0.1, -0.3], [0.45, -0.65], [0.2, 0.7]]
+    out = {}
+    for graphs in (0, 1):
+        h = ss.Handle(n_b_max=6, s_b_max=64, max_points=2, max_inj=2, precision=prec, use_graphs=graphs)
+        res, calls = [], []
+        try:
+            h.set_device(0, dev)
+            for Es in batches:
+                c0 = h.host_launch_count()
+                xs, st, _ = h.solve(Es, [0, 0], inj)
+                T, _, _, _ = h.transmission(Es, [0, 0])
+                calls.append(h.host_launch_count() - c0)
+                res.append((np.asarray(T).copy(), [np.asarray(x).copy() for x in xs], np.asarray(st)))
+        finally:
+            h.close()
+        out[graphs] = (res, calls)
+    for (Ta, xa, sa), (Tb, xb, sb) in zip(out[0][0], out[1][0]):
+        assert np.all(sa == 0) and np.all(sb == 0)
+        assert np.array_equal(Ta, Tb)
+        assert all(np.array_equal(a, b) for a, b in zip(xa, xb))
+    eager_calls, graph_calls = out[0][1], out[1][1]
+    assert graph_calls[2] < 0.1 * eager_calls[2], (eager_calls, graph_calls)

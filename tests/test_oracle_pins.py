@@ -459,3 +459,45 @@ def test_ldos_of_decoupled_wire_closed_form():
         expect = float(np.sum(1.0 / (np.pi * np.sqrt(4 * t * t - (E - eps[inb]) ** 2))))
         rho = dense.ldos(dev, E)
         assert np.allclose(rho, expect, rtol=1e-7, atol=1e-9), (E, rho, expect)
+
+
+# ------------------------------------------------------ modes (FEAST route)
+@pytest.mark.parametrize("s,seed", [(6, 31), (12, 5)])
+@pytest.mark.parametrize("E", [-0.4, 0.7, 3.0])
+def test_mode_self_energies_equal_decimation(s, seed, E):
+    """Sigma from the lead's Bloch modes (all of them inside the annulus) is the
+    same quantity as the decimation's, by an independent route: a generalized
+    eigensolver on the companion pencil instead of the doubling."""
+    from oracle import feast
+    dev = synth.make_device(3, s, seed)[0]
+    sL, sR, _ = leads.self_energies(dev, E)
+    fL, fR, info = feast.self_energies(dev, E)
+    assert info["modes_L"] == s and info["modes_R"] == s
+    assert np.linalg.norm(fL - sL) / np.linalg.norm(sL) < 1e-10
+    assert np.linalg.norm(fR - sR) / np.linalg.norm(sR) < 1e-10
+
+
+@pytest.mark.parametrize("k", [0.4, 1.3, 2.5])
+def test_mode_self_energy_of_chain(k):
+    """s = 1 chain: the right-going mode is lambda = e^{ik}, Sigma = t e^{ik}."""
+    from oracle import feast
+    eps0, t = 0.2, -0.7
+    E = eps0 + 2 * t * math.cos(k)
+    sL, sR, info = feast.self_energies(chain_device(eps0, t), E)
+    assert abs(sR[0, 0] - t * np.exp(1j * k)) < 1e-7 and abs(sL[0, 0] - t * np.exp(1j * k)) < 1e-7
+
+
+def test_mode_counts_and_annulus():
+    """Each direction has s modes; the unimodular ones number twice the open
+    channels; shrinking the annulus drops only fast-decaying modes."""
+    from oracle import feast
+    s, t = 10, -0.8
+    dev, eps = synth.decoupled_wire(s, 3, t, seed=4)
+    cell = (dev.H_diag[0], dev.H_up[0], dev.S_diag[0], dev.S_up[0])
+    E = 0.05
+    lam, u = feast.lead_modes(cell, E + 1j * leads.DEFAULT_ETA)
+    assert np.sum(np.abs(lam) < 1) == s and np.sum(np.abs(lam) > 1) == s
+    assert np.sum(np.abs(np.abs(lam) - 1) < 1e-6) == 2 * channels.open_channels(cell, E)[0]
+    g_all, m_all = feast.surface_gf(cell, E + 1j * leads.DEFAULT_ETA, "R")
+    g_cut, m_cut = feast.surface_gf(cell, E + 1j * leads.DEFAULT_ETA, "R", R=4.0)
+    assert m_all == s and m_cut == int(np.sum((np.abs(lam) < 1) & (np.abs(lam) > 0.25)))
