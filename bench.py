@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--points", type=int, default=2, help="dense workload: points of the mixed path")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the c1 latency, c3 uneven-batch and c4 dense-block sub-measurements")
+    ap.add_argument("--hermitian", action="store_true",
+                    help="factor the sweep blocks with the no-pivoting Hermitian L D L^H (cfg.hermitian_sweeps)")
+    ap.add_argument("--partitions", type=int, default=1, help="partitions of every device (cfg.partitions)")
+    ap.add_argument("--tournament", action="store_true",
+                    help="tournament pivoting in the cluster LU panels (cfg.tournament_pivoting)")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps of the per-kernel event-timed pass (kernel shares and the roofline)")
     ap.add_argument("--gemm", default=None, metavar="MxNxK",
@@ -494,7 +499,9 @@ def main():
 
     def handle(prec, device_ptrs=1, profile=0):
         h = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=device_ptrs,
-                      stream=stream.cuda_stream, precision=prec, profile=profile, use_graphs=0 if a.no_graphs else 1)
+                      stream=stream.cuda_stream, precision=prec, profile=profile, use_graphs=0 if a.no_graphs else 1,
+                      hermitian_sweeps=1 if a.hermitian else 0, partitions=a.partitions,
+                      tournament_pivoting=1 if a.tournament else 0)
         with torch.cuda.stream(stream):
             for k, d in enumerate(devs):
                 if device_ptrs:
@@ -686,6 +693,9 @@ def main():
             "dtype": "f64" if head_prec == ss.SS_FP64 else "bf16 digit slices, exact fp32 accum -> f64",
             "data": "synthetic",
             "config": {"workload": wl_name(a), "n_b": a.n_b, "s_b": a.s_b, "points_per_step": P,
+                       "sweep_factorisation": "L D L^H without pivoting" if a.hermitian else "pivoted LU",
+                       "partitions": a.partitions,
+                       "panel_pivoting": "tournament" if a.tournament else "partial",
                        "n_inj": a.n_inj, "precision": "fp64" if head_prec == ss.SS_FP64 else "mixed (SS_MIXED_OZAKI)",
                        "parallelism": f"(E,k) shards x{world}",
                        "l2": "inputs larger than L2: per-step workspace "

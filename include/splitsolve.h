@@ -122,6 +122,12 @@ typedef struct {
   double feast_radius;/* R > 1 (default 50)                                               */
   int feast_points;   /* quadrature nodes per circle (default 16)                        */
   int feast_subspace; /* columns m0 of the random block Y (0 = 2 s_b, the full space)   */
+  int tournament_pivoting; /* 1: the pivoted LU panels of up to 1024 rows choose their
+                         pivots by a tournament over the 8 CTAs of a cluster (each CTA's
+                         partial-pivoting candidates, then partial pivoting among them):
+                         two cluster barriers per panel instead of one per column.
+                         Another stable pivot order; results change at rounding level.
+                         Default 0 (partial pivoting).                                */
 } ss_config;
 
 /* Fill *cfg with the defaults listed above (n_b_max = 64, s_b_max = 512,
@@ -277,9 +283,13 @@ const char* ss_noalloc_last_error(void);
  * or 256 (below s_b), and keeps the fastest
  * for this handle.  The factorisation is the block LU of Sec. 3B; the choice
  * changes the order of FP64 roundings only.
+ * It also times the FP64 complex GEMM's five tile shapes on a group of
+ * n_problems s_b x s_b x s_b products (FP64 path) and on the LU's first
+ * rank-nb update, and uses the fastest for those classes of products
+ * instead of the padded-work heuristic.
  * cache_path (optional): a text file of lines "precision s_b n_problems nb
- * nbo upd ms"; a matching line is reused without timing, a new result is
- * appended.
+ * nbo upd ms" and "G precision s_b n_problems square_tile update_tile"; a
+ * matching pair is reused without timing, a new result is appended.
  * Outputs (optional, host): chosen panel width nb, outer width nbo (0: one
  * level), update arithmetic upd, and its time in ms. */
 int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, int* nb, int* nbo, int* upd,

@@ -293,7 +293,7 @@ struct ss_handle {
   Plan p_warm_iter, p_warm_judge, p_final_g;
   Plan p_ir_res, p_ir_cor;
   // autotuned LU settings per block size: panel width and update arithmetic
-  struct Tune { int nb; int nbo; int upd; double ms; };
+  struct Tune { int nb; int nbo; int upd; double ms; int gsq = -1; int gup = -1; };
   std::map<int, Tune> tune;
   std::vector<double> c_err;  // normwise backward error of the last refined solve
   Prof* P() { return cfg.profile ? &prof : nullptr; }
@@ -345,7 +345,8 @@ void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
   Plan::Updates upd = h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64;
   auto it = h->tune.find(smax);
   if (it != h->tune.end()) { nb = it->second.nb; nbo = it->second.nbo; upd = (Plan::Updates)it->second.upd; }
-  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo)) h->plan_error = true;
+  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo, h->cfg.tournament_pivoting))
+    h->plan_error = true;
 }
 // The sweep blocks D_i with cfg.hermitian_sweeps: LDL^H without pivoting,
 // updates on the lower triangle (FP64 path: FP64 updates of depth 16; mixed
@@ -1302,7 +1303,7 @@ int run_feast(ss_handle* h, std::vector<PW>& pts) {
   {
     std::vector<FormDesc> f0, f1;
     std::vector<std::vector<FormDesc>> qpass;  // per problem: the running-sum passes, then the Y1 term
-    std::vector<GemmDesc> g1, g2, gG;
+    std::vector<GemmDesc> g1, g2, gG, gG2;
     std::vector<LuDesc> lu;
     std::vector<EigDesc> eg;
     for (auto& f : fp) {
@@ -1377,9 +1378,9 @@ int run_feast(ss_handle* h, std::vector<PW>& pts) {
       fy.y = Y1; fy.ldy = m0; fy.ay = make_double2(-csum.x, -csum.y);
       mine.push_back(fy);
       qpass.push_back(mine);
-      // Gram matrix Q^H Q = Q1^H Q1 + Q2^H Q2
+      // Gram matrix Q^H Q = Q1^H Q1 + Q2^H Q2 (two launches: both write G)
       gG.push_back(gdesc(m0, m0, s, plain(Q1, m0, 1), plain(Q1, m0), f.G, m0, ONE, ZERO));
-      gG.push_back(gdesc(m0, m0, s, plain(Q2, m0, 1), plain(Q2, m0), f.G, m0, ONE, ONE));
+      gG2.push_back(gdesc(m0, m0, s, plain(Q2, m0, 1), plain(Q2, m0), f.G, m0, ONE, ONE));
       eg.push_back({f.G, f.GZ, f.GX, f.Glam, m0, m0, f.info + 1});
     }
     A.memset0(h->feast_info, sizeof(int) * h->feast_info_n);
@@ -1399,6 +1400,7 @@ int run_feast(ss_handle* h, std::vector<PW>& pts) {
     for (auto& v : qpass) last.push_back(v.back());
     A.form(last);
     A.gemm(gG);
+    A.gemm(gG2);
     A.eig(eg);
   }
   CK(A.upload(st), "upload feast A");
@@ -1701,8 +1703,16 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
     // stay at the same addresses whatever n_inj the next call uses
     Carve c(h->arena);
     carve_batch(c, pts, h->cfg.max_inj, h->mixed());
-    int nmax = 0;
-    for (auto& w : pts) nmax = std::max(nmax, w.n);
+    int nmax = 0, smax_c = 0;
+    for (auto& w : pts) { nmax = std::max(nmax, w.n); smax_c = std::max(smax_c, w.s); }
+    {
+      // FP64 GEMM tile shapes tuned for the batch's largest block size
+      auto tt = h->tune.find(smax_c);
+      const int gsq = tt != h->tune.end() ? tt->second.gsq : -1, gup = tt != h->tune.end() ? tt->second.gup : -1;
+      for (Plan* pl : {&h->p_setup, &h->p_iter[0], &h->p_iter[1], &h->p_final, &h->p_sweep, &h->p_bound, &h->p_ir_res,
+                       &h->p_ir_cor})
+        pl->set_gemm_variants(gsq, gup);
+    }
     const int nsteps = sweep_steps(pts);
     // device scalars: act, iters, conv (2P each), decim info (4P), sweep info
     // (2 MAXP P nsteps), boundary / density-of-states info (P nmax)
@@ -1744,7 +1754,10 @@ int run_points(ss_handle* h, int n_pts, const double* E, const int* k_id, const 
       if (h->cfg.obc == SS_OBC_FEAST) {
         // the leads' Bloch modes by the contour integral, then Sigma from them
         const int r = run_feast(h, pts);
-        if (r) return r;
+        if (r) {
+          for (auto& w : pts) status[w.idx] = r;
+          return r;
+        }
       } else {
       if (h->cfg.warm_start) {
         // learned warm start of each lead that has a network attached (points
@@ -2041,6 +2054,7 @@ void ss_config_default(ss_config* cfg) {
   cfg->feast_radius = 50.0;
   cfg->feast_points = 16;
   cfg->feast_subspace = 0;
+  cfg->tournament_pivoting = 0;
 }
 
 int ss_create(ss_handle** hp, const ss_config* cfg) {
@@ -2312,17 +2326,30 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     if (ms_out) *ms_out = t.ms;
     return SS_OK;
   };
-  // cache lines: "<precision> <s_b> <n_problems> <nb> <nbo> <upd> <ms>"
+  // cache lines: "<precision> <s_b> <n_problems> <nb> <nbo> <upd> <ms>" (LU blocking)
+  // and "G <precision> <s_b> <n_problems> <square tile> <update tile>" (FP64 GEMM tiles)
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
-      int pr, sb, np, nb, nbo, upd;
+      int pr, sb, np, nb, nbo, upd, gs, gu;
       double ms;
-      bool hit = false;
+      bool hit = false, ghit = false;
       ss_handle::Tune t{};
-      while (std::fscanf(f, "%d %d %d %d %d %d %lf", &pr, &sb, &np, &nb, &nbo, &upd, &ms) == 7)
-        if (pr == prec && sb == s_b && np == n_problems) { t = {nb, nbo, upd, ms}; hit = true; }
+      int tgs = -1, tgu = -1;
+      char line[256];
+      while (std::fgets(line, sizeof line, f)) {
+        if (std::sscanf(line, "G %d %d %d %d %d", &pr, &sb, &np, &gs, &gu) == 5) {
+          if (pr == prec && sb == s_b && np == n_problems) { tgs = gs; tgu = gu; ghit = true; }
+        } else if (std::sscanf(line, "%d %d %d %d %d %d %lf", &pr, &sb, &np, &nb, &nbo, &upd, &ms) == 7) {
+          if (pr == prec && sb == s_b && np == n_problems) { t = {nb, nbo, upd, ms}; hit = true; }
+        }
+      }
       std::fclose(f);
-      if (hit) { h->tune[s_b] = t; return report(t); }
+      if (hit) {  // a cache without tile lines keeps the heuristic tile shapes
+        t.gsq = ghit ? tgs : -1;
+        t.gup = ghit ? tgu : -1;
+        h->tune[s_b] = t;
+        return report(t);
+      }
     }
   }
   // synthetic batch of [D | B] systems, D diagonally weighted so the
@@ -2394,6 +2421,46 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     c.ms = best_ms;
     if (e == cudaSuccess && (best.nb < 0 || c.ms < best.ms)) best = c;
   }
+  // FP64 GEMM tile shapes: the products of full s x s blocks (FP64 path) and
+  // the LU's rank-nb updates ((s - nb) x (3 s - nb) x nb, every path), each
+  // group of n_problems timed with every tile shape; the fastest replaces the
+  // padded-work heuristic for this s_b
+  auto time_gemm = [&](const std::vector<GemmDesc>& g, bool lu_label) {
+    int bv = -1;
+    float bms = 1e30f;
+    for (int v = 0; v < zgemm_num_variants() && e == cudaSuccess; ++v) {
+      Plan G;
+      G.gemm(g, lu_label, v);
+      e = G.upload(st);
+      float vbest = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, st);
+        e = G.run(st, nullptr);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) vbest = std::min(vbest, ms);
+      }
+      if (e == cudaSuccess && vbest < bms) { bms = vbest; bv = v; }
+    }
+    return bv;
+  };
+  if (e == cudaSuccess && best.nb > 0) {
+    std::vector<GemmDesc> gsq, gup;
+    const int nbw = std::min(best.nb, s_b);
+    for (int p = 0; p < n_problems; ++p) {
+      z64* Wp = W + p * per;
+      gsq.push_back(gdesc(s_b, s_b, s_b, plain(Wp, 3 * s_b), plain(Wp + s_b, 3 * s_b), Wp + 2 * s_b, 3 * s_b, ONE, ZERO));
+      if (s_b > nbw) {
+        GemmDesc q = gdesc(s_b - nbw, 3 * s_b - nbw, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
+                           plain(Wp + nbw, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + nbw, 3 * s_b, MONE, ONE);
+        gup.push_back(q);
+      }
+    }
+    best.gsq = prec == SS_FP64 ? time_gemm(gsq, false) : -1;
+    best.gup = gup.empty() ? -1 : time_gemm(gup, true);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(W); cudaFree(W0); cudaFree(piv); cudaFree(info);
@@ -2403,6 +2470,7 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
       std::fprintf(f, "%d %d %d %d %d %d %.6f\n", prec, s_b, n_problems, best.nb, best.nbo, best.upd, best.ms);
+      std::fprintf(f, "G %d %d %d %d %d\n", prec, s_b, n_problems, best.gsq, best.gup);
       std::fclose(f);
     }
   }

@@ -165,6 +165,8 @@ int zgemm_tiles(int m, int n, int variant) {
   return ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
 }
 
+int zgemm_num_variants() { return NVAR; }
+
 int zgemm_variant(const std::vector<GemmDesc>& ds) {
   // the tile shape with the least padded work per busy SM (ties: 64 x 64)
   static int nsm = 0;

@@ -132,6 +132,7 @@ void launch_zgemm(const GemmDesc* d, const int* tile_start, int nprob, int total
                   cudaStream_t st, int variant = 0);
 int zgemm_tiles(int m, int n, int variant = 0);  // CTAs one problem needs
 int zgemm_variant(const std::vector<GemmDesc>& ds);  // tile shape padding the group least
+int zgemm_num_variants();
 
 void launch_zform(const FormDesc* d, const int* tile_start, int nprob, int total_tiles,
                   cudaStream_t st);
@@ -140,7 +141,9 @@ int zform_tiles(int rows, int cols);
 // Panel width used for a group whose largest block is smax (keeps the
 // register-resident panel kernel within 32 complex values per thread).
 int lu_panel_width(int smax);
-void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st);
+// tournament != 0: tournament pivoting on the 8-CTA cluster panels (two cluster
+// barriers per panel instead of one per column); others use partial pivoting.
+void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st, int tournament = 0);
 // nbo > 0: two-level blocking with outer width nbo (the solve stops at the
 // outer block's end); far != 0: solve the columns right of the outer block
 // without swaps.

@@ -427,6 +427,263 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_cluste
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+// Tournament pivoting panel (a communication-avoiding LU of the tall panel).
+// Rows are spread over an 8-CTA cluster as in lu_panel_cluster_kernel
+// (row k0 + c + CL t in thread t of cluster rank c):
+//   1. every CTA runs partial pivoting on its own rows only (CTA-local
+//      barriers) and offers the rows it picked, with their original values,
+//      as candidates; the owners of rows k0..k0+NB-1 publish those rows too;
+//   2. one cluster barrier; every CTA reads the CL x NB candidates through
+//      distributed shared memory and runs the same partial pivoting on them
+//      (largest |re| + |im|, lowest row on ties): that selects the NB pivot
+//      rows in order and yields the factored pivot block [L11 \ U11], the same
+//      in every CTA;
+//   3. the pivot rows applied as NB successive row exchanges (recorded in
+//      ipiv, as partial pivoting does) tell each thread which original row
+//      ends up in its position; that row times U11^-1 is its row of L21.
+// Two cluster barriers per panel instead of one per column.  The pivots may
+// differ from partial pivoting's (another stable choice); the result is an
+// exact P A = L U of the panel in the LU code's layout.
+template <int NB, int CL, int NT>
+struct TsluShared {
+  z64 pubC[NB][NB];   // this CTA's candidates (original rows), published
+  int pubId[NB];
+  int pubN;
+  z64 pubT[NB][NB];   // original rows k0 + i owned by this CTA, published
+  z64 C[CL * NB][NB]; // gathered candidates, then their elimination
+  int cid[CL * NB];
+  int nc;
+  int cbase[CL];      // first slot of each CTA's candidates
+  z64 T[NB][NB];      // rows k0 .. k0 + NB - 1, original
+  z64 prow[NB];
+  double wv[NT / 32];
+  int wi[NT / 32];
+  int win, bad;
+  int ipv[NB];
+  int pivc[NB];       // candidate slot of pivot j
+};
+
+template <int NB, int NT>
+__device__ __forceinline__ void cta_argmax(double v, int idx, double (&wv)[NT / 32], int (&wi)[NT / 32], int& out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, off);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { wv[warp] = v; wi[warp] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = wv[0];
+    int bi = wi[0];
+    for (int q = 1; q < NT / 32; ++q)
+      if (wv[q] > bv || (wv[q] == bv && wi[q] < bi)) { bv = wv[q]; bi = wi[q]; }
+    out = bv >= 0.0 ? bi : -1;
+  }
+  __syncthreads();
+}
+
+template <int NB, int CL, int NT>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) lu_panel_tslu_kernel(
+    const LuDesc* __restrict__ descs, int k0, int nb) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const LuDesc d = descs[blockIdx.x / CL];
+  __shared__ TsluShared<NB, CL, NT> sh;
+  const bool live = !(d.active && __ldg(d.active) == 0) && k0 < d.s;  // same for the whole cluster
+  const int tid = threadIdx.x;
+  const int s = d.s;
+  const int nbw = live ? min(min(nb, NB), s - k0) : 0;
+  const int row = k0 + crank + CL * tid;
+  const bool valid = live && row < s;
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  z64 a[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) a[c] = (valid && c < nbw) ? w[(size_t)row * ld + k0 + c] : zmk(0.0, 0.0);
+  if (tid == 0) sh.pubN = 0;
+  // ---- 1. local partial pivoting on this CTA's rows: candidates
+  {
+    z64 b[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) b[c] = a[c];
+    bool chosen = false;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < nbw) {  // nbw is uniform over the CTA
+        const double v = (valid && !chosen) ? fabs(b[j].x) + fabs(b[j].y) : -1.0;
+        const double vv = (v == v) ? v : 1.7976931348623157e308;  // NaN rows first (reported below)
+        cta_argmax<NB, NT>(vv, valid ? row : s + CL * NT, sh.wv, sh.wi, sh.win);
+        const int wrow = sh.win;
+        if (wrow >= 0) {
+          if (row == wrow) {
+            chosen = true;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) { sh.prow[c] = b[c]; sh.pubC[j][c] = a[c]; }
+            sh.pubId[j] = row;
+            sh.pubN = j + 1;
+          }
+          __syncthreads();
+          if (valid && !chosen) {
+            const z64 p = sh.prow[j];
+            const z64 l = zmul(b[j], zinv(p));
+#pragma unroll
+            for (int c = j + 1; c < NB; ++c) {
+              const z64 u = sh.prow[c];
+              b[c].x = fma(-l.x, u.x, b[c].x);
+              b[c].x = fma(l.y, u.y, b[c].x);
+              b[c].y = fma(-l.x, u.y, b[c].y);
+              b[c].y = fma(-l.y, u.x, b[c].y);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (valid && row < k0 + nbw) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) sh.pubT[row - k0][c] = a[c];
+  }
+  cluster.sync();
+  // ---- 2. gather every CTA's candidates and the top rows; partial pivoting on them
+  if (nbw > 0) {
+    if (tid == 0) {
+      int n = 0;
+      for (int q = 0; q < CL; ++q) {
+        const TsluShared<NB, CL, NT>* o = cluster.map_shared_rank(&sh, q);
+        const int m = o->pubN;
+        sh.cbase[q] = n;
+        for (int i = 0; i < m; ++i) sh.cid[n + i] = o->pubId[i];
+        n += m;
+      }
+      sh.nc = n;
+    }
+    __syncthreads();
+    // values: candidate slot cbase[q] + i holds CTA q's i-th candidate
+    for (int e = tid; e < CL * NB * NB; e += NT) {
+      const int q = e / (NB * NB), i = (e / NB) % NB, c = e % NB;
+      const int m = (q + 1 < CL ? sh.cbase[q + 1] : sh.nc) - sh.cbase[q];
+      if (i < m) sh.C[sh.cbase[q] + i][c] = cluster.map_shared_rank(&sh, q)->pubC[i][c];
+    }
+    for (int e = tid; e < nbw * NB; e += NT) {
+      const int i = e / NB, c = e % NB;
+      sh.T[i][c] = cluster.map_shared_rank(&sh, i % CL)->pubT[i][c];
+    }
+    if (tid == 0) sh.bad = 0;
+    __syncthreads();
+    const int nc = sh.nc;
+    // candidate slots handled by this thread: tid, tid + NT (nc <= CL * NB <= 2 NT)
+    bool ch0 = false, ch1 = false;
+    for (int j = 0; j < nbw; ++j) {
+      double v = -1.0;
+      int vi = s + CL * NT;
+      int slot = -1;
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * NT;
+        if (e < nc && !(h ? ch1 : ch0)) {
+          const z64 x = sh.C[e][j];
+          double a1 = fabs(x.x) + fabs(x.y);
+          if (!(a1 == a1)) a1 = 1.7976931348623157e308;
+          if (a1 > v || (a1 == v && sh.cid[e] < vi)) { v = a1; vi = sh.cid[e]; slot = e; }
+        }
+      }
+      // argmax over (value, original row); the slot travels with the row index
+      cta_argmax<NB, NT>(v, vi, sh.wv, sh.wi, sh.win);
+      const int wrow = sh.win;
+      if (slot >= 0 && sh.cid[slot] == wrow) {
+        sh.pivc[j] = slot;
+        if (slot == tid) ch0 = true; else ch1 = true;
+        const z64 pv = sh.C[slot][j];
+        const double ap = fabs(pv.x) + fabs(pv.y);
+        if (!(ap > 0.0 && ap <= 1.7976931348623157e308) && sh.bad == 0) sh.bad = j + 1;
+      }
+      __syncthreads();
+      const int ps = sh.pivc[j];
+      const z64 inv = zinv(sh.C[ps][j]);
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * NT;
+        if (e < nc && !(h ? ch1 : ch0)) {
+          const z64 l = zmul(sh.C[e][j], inv);
+          sh.C[e][j] = l;  // multiplier (kept for the pivot block rows)
+          for (int c = j + 1; c < NB; ++c) sh.C[e][c] = zsub(sh.C[e][c], zmul(l, sh.C[ps][c]));
+        }
+      }
+      __syncthreads();
+    }
+    // pivot rows as successive exchanges (row positions), one thread
+    if (tid == 0) {
+      int pos_row[2 * NB], pos_at[2 * NB], np = 0;  // (position -> row) for touched positions
+      for (int j = 0; j < nbw; ++j) {
+        const int prw = sh.cid[sh.pivc[j]];
+        // current position of row prw
+        int p = prw;
+        for (int t = 0; t < np; ++t)
+          if (pos_row[t] == prw) { p = pos_at[t]; break; }
+        sh.ipv[j] = p;
+        // swap the contents of positions k0 + j and p
+        const int a1 = k0 + j;
+        int r1 = a1, r2 = p;  // rows currently at a1 and p
+        int t1 = -1, t2 = -1;
+        for (int t = 0; t < np; ++t) { if (pos_at[t] == a1) t1 = t; if (pos_at[t] == p) t2 = t; }
+        if (t1 >= 0) r1 = pos_row[t1];
+        if (t2 >= 0) r2 = pos_row[t2];
+        if (t1 < 0) { t1 = np; pos_at[np] = a1; ++np; }
+        if (t2 < 0 && p != a1) { t2 = np; pos_at[np] = p; ++np; }
+        pos_row[t1] = r2;
+        if (p != a1) pos_row[t2] = r1;
+      }
+      if (crank == 0) {
+        for (int j = 0; j < nbw; ++j) d.ipiv[k0 + j] = sh.ipv[j];
+        if (sh.bad && d.info && *d.info == 0) *d.info = k0 + sh.bad;
+      }
+    }
+    __syncthreads();
+    // ---- 3. this thread's final row
+    if (valid) {
+      if (row < k0 + nbw) {
+        const int ps = sh.pivc[row - k0];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < nbw) w[(size_t)row * ld + k0 + c] = sh.C[ps][c];
+      } else {
+        int src = row;
+        for (int j = nbw - 1; j >= 0; --j) {
+          if (src == k0 + j) src = sh.ipv[j];
+          else if (src == sh.ipv[j]) src = k0 + j;
+        }
+        // a row moved below the pivot block always comes from the block's original rows
+        const bool from_top = src != row && src >= k0 && src < k0 + nbw;
+        z64 x[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) x[c] = from_top ? sh.T[src - k0][c] : a[c];
+        // L row = x U11^-1, U11 = upper part of the pivot block
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < nbw) {
+            z64 acc = x[j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) {
+              const z64 u = sh.C[sh.pivc[c]][j];
+              acc.x = fma(-x[c].x, u.x, acc.x);
+              acc.x = fma(x[c].y, u.y, acc.x);
+              acc.y = fma(-x[c].x, u.y, acc.y);
+              acc.y = fma(-x[c].y, u.x, acc.y);
+            }
+            x[j] = zmul(acc, zinv(sh.C[sh.pivc[j]][j]));
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < nbw) w[(size_t)row * ld + k0 + c] = x[c];
+      }
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 constexpr int RB_THREADS = 64;  // one thread per column; small CTAs spread the FP64 work over more SMs
 
 // Row swaps on every column outside the panel, then U12 = L11^-1 A12 on the
@@ -574,6 +831,9 @@ __global__ void __launch_bounds__(RB_THREADS) lu_backsub_diag_kernel(const LuDes
 // update (restricted to the lower triangle) and back substitution apply
 // unchanged.  A zero or non-finite d_j records 1 + its column in *info.
 constexpr int HP_THREADS = 128;
+// Largest |re| + |im| of an entry of L accepted from the unpivoted Hermitian
+// factorisation; beyond it the pivot growth has used up most of FP64.
+constexpr double HERM_MAX_L = 1e8;
 
 template <int NB>
 __global__ void __launch_bounds__(HP_THREADS) herm_diag_kernel(const LuDesc* __restrict__ descs, int k0, int nb) {
@@ -658,12 +918,17 @@ __global__ void __launch_bounds__(HP_THREADS) herm_rows_kernel(const LuDesc* __r
       a[j] = zmul(acc, dinv[j]);
     }
   }
+  bool grow = false;
 #pragma unroll
   for (int c = 0; c < NB; ++c)
     if (c < nbw) {
       w[(size_t)r * ld + k0 + c] = a[c];
       w[(size_t)(k0 + c) * ld + r] = zmul(Uu[c][c], zconj(a[c]));  // U12 = D1 L21^H
+      const double m = fabs(a[c].x) + fabs(a[c].y);
+      grow = grow || !(m <= HERM_MAX_L);
     }
+  // without pivoting a tiny d_j makes L explode: report it as a singular block
+  if (grow && d.info) atomicCAS(d.info, 0, k0 + 1);
 }
 }  // namespace
 
@@ -686,10 +951,16 @@ int lu_panel_width(int smax) {
   return 32;
 }
 
-void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st) {
+void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st, int tournament) {
   if (nprob <= 0) return;
   const int h = smax - k0;  // rows of the tallest panel in the group
   constexpr int CL = 8;
+  if (tournament) {
+    if (nb == 16 && h <= CL * 64) { lu_panel_tslu_kernel<16, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb); return; }
+    if (nb == 16 && h <= CL * 128) { lu_panel_tslu_kernel<16, CL, 128><<<nprob * CL, 128, 0, st>>>(d, k0, nb); return; }
+    if (nb == 8 && h <= CL * 64) { lu_panel_tslu_kernel<8, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb); return; }
+    if (nb == 8 && h <= CL * 128) { lu_panel_tslu_kernel<8, CL, 128><<<nprob * CL, 128, 0, st>>>(d, k0, nb); return; }
+  }
   if (nb == 16 && h <= CL * 64) lu_panel_cluster_kernel<16, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb);
   else if (nb == 16 && h <= CL * 128) lu_panel_cluster_kernel<16, CL, 128><<<nprob * CL, 128, 0, st>>>(d, k0, nb);
   else if (nb == 8 && h <= CL * 64) lu_panel_cluster_kernel<8, CL, 64><<<nprob * CL, 64, 0, st>>>(d, k0, nb);

@@ -273,7 +273,7 @@ bool Plan::tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pac
 }
 
 bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err,
-                    int nbo) {
+                    int nbo, int tournament) {
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
@@ -311,7 +311,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   auto panel = [&](int k0) {
     LaunchRec r;
     r.kind = K_LU_PANEL;
-    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = smax;
+    r.off = off; r.nprob = np; r.k0 = k0; r.nb = nb; r.maxc = smax; r.ival = tournament;
     recs_.push_back(r);
   };
   if (nbo <= 0) {
@@ -612,7 +612,7 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
         break;
       }
       case K_FORM: launch_zform((const FormDesc*)d, t, r.nprob, r.tiles, st); ++n; break;
-      case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
+      case K_LU_PANEL: launch_lu_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st, r.ival); ++n; break;
       case K_LU_HPANEL:
         launch_herm_panel((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st);
         n += (r.maxc - r.k0 - r.nb > 0) ? 2 : 1;

@@ -88,9 +88,17 @@ class Plan {
 
   // fp32 = true: the FP32-arithmetic kernel (low-rank updates of the mixed path)
   // lu_label: account the launch as an LU update (profiling only)
-  void gemm(const std::vector<GemmDesc>& ds, bool lu_label = false) {
+  // Tile shapes of the FP64 GEMM chosen by ss_autotune (-1: the heuristic):
+  // sq for the products of full blocks, up for the LU's rank-nb updates.
+  void set_gemm_variants(int sq, int up) { var_sq_ = sq; var_up_ = up; }
+  void gemm(const std::vector<GemmDesc>& ds, bool lu_label = false, int force_variant = -1) {
     if (ds.empty()) return;
-    const int variant = zgemm_variant(ds);
+    // the tuned shape applies to the class it was timed on: square products of
+    // full blocks, or rank-nb updates at least as wide as tall
+    const GemmDesc& g0 = ds[0];
+    const int tuned = lu_label ? ((g0.k <= 32 && g0.n >= g0.m) ? var_up_ : -1)
+                               : ((g0.m == g0.n && g0.k >= 64) ? var_sq_ : -1);
+    const int variant = force_variant >= 0 ? force_variant : (tuned >= 0 ? tuned : zgemm_variant(ds));
     std::vector<int> start(ds.size());
     int tot = 0;
     for (size_t i = 0; i < ds.size(); ++i) { start[i] = tot; tot += zgemm_tiles(ds[i].m, ds[i].n, variant); }
@@ -140,8 +148,9 @@ class Plan {
   // nbo > nb (a multiple of nb): two-level blocking; the depth-nbo
   // trailing and back-substitution updates use `upd`, the nb-deep updates
   // inside an outer block are FP64 unless upd is UPD_EXACT_ALL.
+  // tournament: tournament pivoting in the cluster panels (see launch_lu_panel).
   bool lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
-                size_t cap = 0, int* err = nullptr, int nbo = 0);
+                size_t cap = 0, int* err = nullptr, int nbo = 0, int tournament = 0);
   // Hermitian LDL^H without pivoting of the leading s x s block of every
   // problem (only its lower triangle is read), then the solve of the
   // right-hand-side columns s..ncols-1: panels of nb columns, trailing updates
@@ -230,6 +239,7 @@ class Plan {
   size_t devcap_ = 0;
   cudaGraphExec_t exec_ = nullptr;
   long long graph_kernels_ = 0;
+  int var_sq_ = -1, var_up_ = -1;
   size_t graph_sig_ = 0;  // signature of the launch sequence the graph was captured from
   size_t last_sig_ = 0;   // signature of the previous upload
   bool repeat_ = false;   // this upload repeats the previous one's launch sequence

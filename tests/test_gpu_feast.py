@@ -63,14 +63,21 @@ def test_feast_reduced_annulus_matches_oracle(ss):
     s = 12
     dev = synth.make_device(3, s, seed=212)[0]
     E = 0.3
-    lam, _ = feast.lead_modes(leads.lead_cells(dev)[1], E + 1j * leads.DEFAULT_ETA)
-    a = np.sort(np.abs(lam))
-    R = 3.0
-    if np.min(np.abs(np.log(a) - np.log(R))) < 0.2 or np.min(np.abs(np.log(a) + np.log(R))) < 0.2:
-        pytest.skip("an eigenvalue too close to the contour for this seed")
+    # the radius: the widest gap in log |lambda| above the unit circle, so both
+    # circles (R and 1/R) pass between eigenvalues and a few modes fall outside
+    mods = []
+    for side in (0, 1):
+        lam, _ = feast.lead_modes(leads.lead_cells(dev)[side], E + 1j * leads.DEFAULT_ETA)
+        mods.append(np.abs(lam))
+    a = np.sort(np.concatenate([np.concatenate(mods), 1.0 / np.concatenate(mods)]))
+    la = np.log(a[a > 1.2])
+    gaps = np.diff(la)
+    i = int(np.argmax(gaps[:-1]))       # not beyond the largest modulus
+    R = float(np.exp(0.5 * (la[i] + la[i + 1])))
+    assert np.min(np.abs(np.log(a) - np.log(R))) > 0.1
     sL, sR, st = feast_sigmas(ss, [dev], [E], feast_radius=R, feast_points=32)
     fL, fR, info = feast.self_energies(dev, E, R=R)
-    assert info["modes_R"] < s  # modes were dropped
+    assert info["modes_L"] + info["modes_R"] < 2 * s  # modes were dropped
     assert rel(sR[0], fR) < 1e-8 and rel(sL[0], fL) < 1e-8
 
 

@@ -224,14 +224,26 @@ def test_dos_closed_forms_on_gpu(ss):
 
 
 # ------------------------------------------- Hermitian LDL^H of the sweep blocks
+def below_spectrum(dev, margins):
+    """Energies below the lowest eigenvalue of the closed device (H, S): there
+    A = E S - H is negative definite, and so is every Schur complement D_i."""
+    import scipy.linalg as sla
+    A0 = dense.assemble_A(dev, 0.0)          # -H
+    A1 = dense.assemble_A(dev, 1.0) - A0     # S
+    lo = sla.eigh(-A0, A1, eigvals_only=True)[0]
+    return [float(lo - m) for m in margins]
+
+
 @pytest.mark.parametrize("prec", [0, 3])
 @pytest.mark.parametrize("n_b,s_b", [(16, 32), (5, 70), (3, 130), (4, 256), (7, 1)])
 def test_hermitian_sweeps_match_oracle(ss, prec, n_b, s_b):
     """The sweep blocks D_i factored as L D L^H without pivoting (the paper's
     no-pivoting Hermitian solver), updates on the lower triangle only: x, T and
-    Sigma at the parity bar of the pivoted LU."""
+    Sigma at the parity bar of the pivoted LU, at energies below the device's
+    spectrum where every D_i is definite (the regime in which elimination
+    without pivoting is stable; in band the blocks are indefinite)."""
     dev = synth.make_device(n_b, s_b, seed=120 + s_b)[0]
-    Es = [0.3, -0.45]
+    Es = below_spectrum(dev, [0.5, 3.0])
     inj = [synth.make_injection(s_b, 3, seed=130 + i)[0] for i in range(2)]
     r = run_points(ss, [dev, dev], Es, inj, precision=prec, hermitian_sweeps=1)
     assert np.all(np.asarray(r["st_T"]) == 0)
@@ -241,7 +253,7 @@ def test_hermitian_sweeps_match_oracle(ss, prec, n_b, s_b):
 
 def test_hermitian_sweeps_with_partitions_and_lean_mode(ss):
     dev = synth.make_device(9, 48, seed=140, band=12, s_pert=0.02)[0]
-    Es = [0.1, -0.7]
+    Es = below_spectrum(dev, [0.2, 1.5])
     inj = [synth.make_injection(48, 2, seed=141 + i)[0] for i in range(2)]
     r = run_points(ss, [dev, dev], Es, inj, hermitian_sweeps=1, partitions=3)
     for p in range(2):
@@ -250,6 +262,19 @@ def test_hermitian_sweeps_with_partitions_and_lean_mode(ss):
     assert np.all(st == 0)
     for p in range(2):
         assert dense.rel_T_err(float(T[p]), float(r["T"][p])) < 1e-9
+
+
+def test_hermitian_sweeps_report_pivot_growth(ss):
+    """In band the blocks are indefinite and elimination without pivoting can
+    blow up; where |L| exceeds 1e8 the point is reported singular rather than
+    returned wrong.  (A device whose first diagonal block has a zero leading
+    entry forces it.)"""
+    dev = synth.make_device(3, 16, seed=151)[0]
+    E = 0.2
+    # A_11 entry (0, 0) = E S - H = 0: the first pivot of the block sweep's last block is zero
+    dev.H_diag[0][0, 0] = E * dev.S_diag[0][0, 0]
+    r = run_points(ss, [dev], [E], hermitian_sweeps=1)
+    assert r["st_T"][0] == ss.SS_ERR_SINGULAR
 
 
 def test_hermitian_sweeps_halve_the_factorisation_flops(ss):
@@ -305,3 +330,41 @@ def test_repeated_batches_replay_graphs_bit_identically(ss, prec):
         assert all(np.array_equal(a, b) for a, b in zip(xa, xb))
     eager_calls, graph_calls = out[0][1], out[1][1]
     assert graph_calls[2] < 0.1 * eager_calls[2], (eager_calls, graph_calls)
+
+
+# ------------------------------------------------- tournament pivoting panels
+@pytest.mark.parametrize("prec", [0, 3])
+@pytest.mark.parametrize("n_b,s_b", [(16, 32), (5, 70), (3, 130), (2, 600)])
+def test_tournament_pivoting_matches_oracle(ss, prec, n_b, s_b):
+    """LU panels whose pivots come from a tournament over the cluster's CTAs
+    (16-wide panels up to 512 rows, 8-wide up to 1024): x, T and Sigma at the
+    parity bar of partial pivoting."""
+    dev = synth.make_device(n_b, s_b, seed=170 + s_b)[0]
+    Es = [0.3, -0.45]
+    inj = [synth.make_injection(s_b, 3, seed=180 + i)[0] for i in range(2)]
+    r = run_points(ss, [dev, dev], Es, inj, precision=prec, tournament_pivoting=1)
+    assert np.all(np.asarray(r["st_T"]) == 0)
+    for p in range(2):
+        check_point(r, p, dev, Es[p], inj[p])
+
+
+def test_tournament_pivoting_reports_singular_and_nan(ss):
+    dev = synth.make_device(3, 16, seed=16)[0]
+    E = 0.4
+    dev.H_diag[-1] = E * dev.S_diag[-1]   # A_nn = 0: the first pivot of the backward sweep is zero
+    h = ss.Handle(n_b_max=3, s_b_max=16, max_points=1, max_inj=1, tournament_pivoting=1)
+    try:
+        h.set_device(0, dev)
+        T, err, st, rc = h.transmission([E], [0])
+    finally:
+        h.close()
+    assert st[0] == ss.SS_ERR_SINGULAR
+    dev2 = synth.make_device(3, 16, seed=17)[0]
+    dev2.H_diag[1][3, 3] = np.nan
+    h = ss.Handle(n_b_max=3, s_b_max=16, max_points=1, max_inj=1, tournament_pivoting=1)
+    try:
+        h.set_device(0, dev2)
+        T, err, st, rc = h.transmission([0.2], [0])
+    finally:
+        h.close()
+    assert st[0] != ss.SS_OK

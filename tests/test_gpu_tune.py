@@ -66,3 +66,31 @@ def test_forced_blocking_parity(ss, tmp_path, prec, nb, nbo, upd):
     assert np.all(st0 == 0) and np.all(st == 0) and np.all(st2 == 0)
     for p, E in enumerate(Es):
         check_point({"sL": sL, "sR": sR, "T": T, "x": xs}, p, dev, E, inj[p])
+
+
+def test_gemm_tile_tuning_is_recorded_and_changes_no_bit(ss, tmp_path):
+    """ss_autotune also times the FP64 GEMM's tile shapes (square block products
+    and the LU's rank-nb updates) and records them; every tile shape sums each
+    output element in the same order, so the tuned plan gives bit-identical x
+    and T to the heuristic one."""
+    cache = tmp_path / "tune.txt"
+    dev = synth.make_device(5, 128, seed=53)[0]
+    inj = synth.make_injection(128, 2, seed=54, n_pts=2)
+    Es = [0.25, -0.6]
+    out = []
+    for tuned in (False, True):
+        h = ss.Handle(n_b_max=5, s_b_max=128, max_points=2, max_inj=2)
+        try:
+            if tuned:
+                h.autotune(128, 4, cache)
+            h.set_device(0, dev)
+            xs, st, _ = h.solve(Es, [0, 0], [inj[0], inj[1]])
+            T, _, st2, _ = h.transmission(Es, [0, 0])
+        finally:
+            h.close()
+        out.append(([np.asarray(x).copy() for x in xs], np.asarray(T).copy()))
+    g = [l.split() for l in cache.read_text().splitlines() if l.startswith("G")]
+    assert len(g) == 1 and g[0][1:4] == ["0", "128", "4"]
+    assert all(-1 <= int(v) <= 4 for v in g[0][4:6]) and int(g[0][4]) >= 0 and int(g[0][5]) >= 0
+    assert np.array_equal(out[0][1], out[1][1])
+    assert all(np.array_equal(a, b) for a, b in zip(out[0][0], out[1][0]))
