@@ -326,6 +326,18 @@ def run_dense(a):
     print(json.dumps(out), flush=True)
 
 
+def tuned_tiles(cache, prec, s_b, n_problems):
+    """FP64 GEMM tile shapes ss_autotune recorded for this size ("G" line of
+    its cache; -1: the padded-work heuristic), or (None, None)."""
+    out = (None, None)
+    if os.path.exists(cache):
+        for line in open(cache):
+            f = line.split()
+            if len(f) == 6 and f[0] == "G" and f[1:4] == [str(prec), str(s_b), str(n_problems)]:
+                out = (int(f[4]), int(f[5]))
+    return out
+
+
 def committed_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, valid
     only while the kernel's source is the one the counters were taken on (the
@@ -511,7 +523,8 @@ def main():
         stream.synchronize()
         # LU panel width and update arithmetic for this s_b, measured once per
         # precision and cached on disk for later handles
-        tune[prec] = h.autotune(a.s_b, 2 * P, os.path.join(tempfile.gettempdir(), "splitsolve_autotune.txt"))
+        cache = os.path.join(tempfile.gettempdir(), "splitsolve_autotune.txt")
+        tune[prec] = h.autotune(a.s_b, 2 * P, cache) + tuned_tiles(cache, prec, a.s_b, 2 * P)
         return h
 
     def step(hh, s, inj, want_x=True):
@@ -712,7 +725,9 @@ def main():
             "host_launch_calls_per_step": head["host_calls_per_step"],
             "clocks": clk.summary(),
             "lu_tune": {("fp64" if k == ss.SS_FP64 else "mixed"): {"panel_width": v[0], "outer_width": v[1],
-                                                                  "update": v[2], "ms": v[3]}
+                                                                  "update": v[2], "ms": v[3],
+                                                                  "fp64_tile_square": v[4],
+                                                                  "fp64_tile_update": v[5]}
                         for k, v in tune.items()},
             "c1": extras.get("c1"),
             "c3": extras.get("c3"),

@@ -278,15 +278,18 @@ const char* ss_noalloc_last_error(void);
  * systems [D | B] (s_b x 3 s_b, the shape of the doubling and sweep
  * systems) for each panel width (8 and 16, or 32 above
  * s_b = 512) and, in SS_MIXED_OZAKI, each update arithmetic (0: FP64 SIMT,
- * 2: exact tensor-core products for the deep updates, 3: for every update)
+ * 2: exact tensor-core products for the deep updates, 4: also for the outer
+ * block's rows right of it, 3: for every update)
  * with one-level blocking or two-level blocking of outer width 32, 64, 128
  * or 256 (below s_b), and keeps the fastest
  * for this handle.  The factorisation is the block LU of Sec. 3B; the choice
  * changes the order of FP64 roundings only.
- * It also times the FP64 complex GEMM's five tile shapes on a group of
- * n_problems s_b x s_b x s_b products (FP64 path) and on the LU's first
- * rank-nb update, and uses the fastest for those classes of products
- * instead of the padded-work heuristic.
+ * It also times the padded-work heuristic and the FP64 complex GEMM's five
+ * tile shapes on a group of n_problems s_b x s_b x s_b products (FP64 path)
+ * and on the LU's wide rank-nb update in the shape the chosen blocking issues
+ * ((s_b - nb) x (3 s_b - nb) x nb for one level, (nbo - nb) x (3 s_b - nbo) x nb
+ * for two), and uses the fastest for those classes of products (-1 in the
+ * cache: the heuristic).
  * cache_path (optional): a text file of lines "precision s_b n_problems nb
  * nbo upd ms" and "G precision s_b n_problems square_tile update_tile"; a
  * matching pair is reused without timing, a new result is appended.
@@ -302,6 +305,8 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
  *   features (n_in = 19): E, cos k, sin k, sin(m pi E), cos(m pi E), m = 1..8;
  *   layers n_in -> width -> width -> n_out, SiLU, mean-squared loss, Adam.
  * FP32 master weights, BF16 copies used by every GEMM, FP32 accumulation.
+ * A tensor-core GEMM whose pipeline wait times out (2 s) sets a flag that the
+ * next ss_mlp_get or ss_mlp_train_step with a loss reports as SS_ERR_CUDA.
  * All network arrays are DEVICE pointers, row-major, unless stated.
  * ------------------------------------------------------------------------ */
 typedef struct ss_mlp ss_mlp;
@@ -326,6 +331,11 @@ int ss_mlp_forward(ss_mlp* net, int B, const float* x, float* y);
  * also one Adam step (beta1 0.9, beta2 0.999, eps 1e-8).  *loss (host, may
  * be NULL) receives the loss of this batch (the call then synchronises). */
 int ss_mlp_train_step(ss_mlp* net, int B, const float* x, const float* t, float lr, double* loss);
+/* GEMMs on the tcgen05 tensor cores (on = 1, the default when width and n_out
+ * are multiples of 8) or on the tiled SIMT kernel (on = 0); both round the
+ * same operands to BF16 and accumulate in FP32.  Errors: SS_ERR_ARG (on = 1
+ * with a width or n_out that is not a multiple of 8). */
+int ss_mlp_use_tensor_cores(ss_mlp* net, int on);
 const char* ss_mlp_last_error(const ss_mlp* net);
 
 /* Transverse momentum k of Hamiltonian k_id (default 0): the value the

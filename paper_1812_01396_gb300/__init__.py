@@ -32,7 +32,7 @@ EXPORTS = ("ss_config_default", "ss_create", "ss_set_hamiltonian", "ss_self_ener
            "ss_profile_reset", "ss_profile_read_issued", "ss_zgemm", "ss_caroli_transmission",
            "ss_caroli_transmission_noalloc", "ss_noalloc_last_error", "ss_mlp_create", "ss_mlp_destroy",
            "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward", "ss_mlp_train_step", "ss_mlp_last_error",
-           "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan", "ss_dos",
+           "ss_mlp_use_tensor_cores", "ss_set_warm_start", "ss_surface_gf", "ss_autotune", "ss_exact_gemm_plan", "ss_dos",
            "ss_set_momentum", "ss_host_launch_count")
 KERNEL_KINDS = {"zgemm": 0, "form": 1, "lu_panel": 2, "lu_row": 3, "lu_back": 4, "norm1": 5, "trace": 6,
                 "check": 7, "fill": 8, "tc_pack_a": 9, "tc_pack_b": 10, "tcgemm": 11, "zgemm32": 12,
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
     lib.ss_mlp_get.argtypes = [vp, C.c_int, C.POINTER(vp)]
     lib.ss_mlp_forward.argtypes = [vp, C.c_int, vp, vp]
     lib.ss_mlp_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, dp]
+    lib.ss_mlp_use_tensor_cores.argtypes = [vp, C.c_int]
     lib.ss_mlp_last_error.argtypes = [vp]
     lib.ss_mlp_last_error.restype = C.c_char_p
     lib.ss_set_warm_start.argtypes = [vp, vp, C.c_int, C.c_double]
@@ -120,7 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.ss_exact_gemm_plan.restype = C.c_int
     lib.ss_surface_gf.argtypes = [vp, C.c_int, dp, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double, vp, ip, ip, ip]
     for name in ("ss_mlp_create", "ss_mlp_destroy", "ss_mlp_set_params", "ss_mlp_get", "ss_mlp_forward",
-                 "ss_mlp_train_step", "ss_set_warm_start", "ss_surface_gf"):
+                 "ss_mlp_train_step", "ss_mlp_use_tensor_cores", "ss_set_warm_start", "ss_surface_gf"):
         getattr(lib, name).restype = C.c_int
     for name in ("ss_create", "ss_set_hamiltonian", "ss_self_energy", "ss_solve", "ss_transmission",
                  "ss_destroy"):
@@ -517,6 +518,11 @@ class MLP:
 
     def get_params(self):
         return self._get(0)
+
+    def use_tensor_cores(self, on):
+        """GEMMs on the tcgen05 tensor cores (default when width and n_out are
+        multiples of 8) or on the SIMT kernel."""
+        self._check(self._lib.ss_mlp_use_tensor_cores(self._n, int(bool(on))))
 
     def get_grads(self):
         return self._get(1)

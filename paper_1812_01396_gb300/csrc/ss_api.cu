@@ -2389,7 +2389,8 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
       cands.push_back({nb, 0, (int)Plan::UPD_EXACT_TC, 0.0});
       for (int nbo : {32, 64, 128, 256})
         if (nbo < s_b && nbo > nb)
-          for (int u : {(int)Plan::UPD_EXACT_TC, (int)Plan::UPD_EXACT_ALL}) cands.push_back({nb, nbo, u, 0.0});
+          for (int u : {(int)Plan::UPD_EXACT_TC, (int)Plan::UPD_EXACT_FAR, (int)Plan::UPD_EXACT_ALL})
+            cands.push_back({nb, nbo, u, 0.0});
     }
   }
   ss_handle::Tune best{-1, 0, 0, 0.0};
@@ -2411,7 +2412,8 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
       e = cudaMemcpyAsync(W, W0, tot * sizeof(z64), cudaMemcpyDeviceToDevice, st);
       cudaEventRecord(e0, st);
-      if (e == cudaSuccess) e = P.run(st, nullptr);
+      // timed as the pipeline runs it: replayed from a CUDA graph (captured on the first run)
+      if (e == cudaSuccess) e = h->cfg.use_graphs ? P.replay(st, nullptr) : P.run(st, nullptr);
       cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -2422,18 +2424,19 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     if (e == cudaSuccess && (best.nb < 0 || c.ms < best.ms)) best = c;
   }
   // FP64 GEMM tile shapes: the products of full s x s blocks (FP64 path) and
-  // the LU's rank-nb updates ((s - nb) x (3 s - nb) x nb, every path), each
-  // group of n_problems timed with every tile shape; the fastest replaces the
-  // padded-work heuristic for this s_b
+  // the LU's wide rank-nb updates in the shape the chosen blocking issues them
+  // (one level: (s - nb) x (3 s - nb) x nb; two levels: the outer block's rows
+  // right of it, (nbo - nb) x (3 s - nbo) x nb), each group of n_problems timed
+  // with the heuristic (-1) and with every tile shape; the fastest is kept
   auto time_gemm = [&](const std::vector<GemmDesc>& g, bool lu_label) {
     int bv = -1;
     float bms = 1e30f;
-    for (int v = 0; v < zgemm_num_variants() && e == cudaSuccess; ++v) {
+    for (int v = -1; v < zgemm_num_variants() && e == cudaSuccess; ++v) {
       Plan G;
       G.gemm(g, lu_label, v);
       e = G.upload(st);
       float vbest = 1e30f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
         cudaEventRecord(e0, st);
         e = G.run(st, nullptr);
         cudaEventRecord(e1, st);
@@ -2452,10 +2455,13 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     for (int p = 0; p < n_problems; ++p) {
       z64* Wp = W + p * per;
       gsq.push_back(gdesc(s_b, s_b, s_b, plain(Wp, 3 * s_b), plain(Wp + s_b, 3 * s_b), Wp + 2 * s_b, 3 * s_b, ONE, ZERO));
-      if (s_b > nbw) {
-        GemmDesc q = gdesc(s_b - nbw, 3 * s_b - nbw, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
-                           plain(Wp + nbw, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + nbw, 3 * s_b, MONE, ONE);
-        gup.push_back(q);
+      if (best.nbo > nbw && best.nbo < s_b) {
+        const int K1 = best.nbo;
+        gup.push_back(gdesc(K1 - nbw, 3 * s_b - K1, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
+                            plain(Wp + K1, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + K1, 3 * s_b, MONE, ONE));
+      } else if (s_b > nbw) {
+        gup.push_back(gdesc(s_b - nbw, 3 * s_b - nbw, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
+                            plain(Wp + nbw, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + nbw, 3 * s_b, MONE, ONE));
       }
     }
     best.gsq = prec == SS_FP64 ? time_gemm(gsq, false) : -1;

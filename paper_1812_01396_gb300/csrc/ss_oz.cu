@@ -387,6 +387,57 @@ __device__ __forceinline__ void write_digits2(__nv_bfloat16* row, int w, int off
   }
 }
 
+// The same digits written to two places: row d0 at off0 (negated when neg0:
+// the digits of -x are exactly the negated digits of x) and row d1 at off1.
+// B' holds every value of op(B) twice ([Br | -Bi] and [Bi | Br]), so its
+// digits are extracted once.
+template <int S>
+__device__ __forceinline__ void write_digits2x(__nv_bfloat16* d0, int off0, bool neg0, __nv_bfloat16* d1, int off1,
+                                               int w, int beta, double x0, double x1, int e) {
+  long long R0 = fixed62(x0, e), R1 = fixed62(x1, e);
+#pragma unroll 3
+  for (int t = 0; t < S; ++t) {
+    const int sh = 62 - beta * (t + 1);
+    long long q0, q1;
+    if (sh > 0) {
+      const long long h = 1ll << (sh - 1);
+      q0 = (R0 + h) >> sh;
+      q1 = (R1 + h) >> sh;
+      R0 -= q0 << sh;
+      R1 -= q1 << sh;
+    } else {
+      q0 = R0 << -sh;
+      q1 = R1 << -sh;
+      R0 = R1 = 0;
+    }
+    const float f0 = (float)(int)q0, f1 = (float)(int)q1;
+    const __nv_bfloat162 v = __floats2bfloat162_rn(f0, f1);
+    *reinterpret_cast<__nv_bfloat162*>(d0 + (size_t)t * w + off0) = neg0 ? __floats2bfloat162_rn(-f0, -f1) : v;
+    *reinterpret_cast<__nv_bfloat162*>(d1 + (size_t)t * w + off1) = v;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void write_digits1x(__nv_bfloat16* d0, int off0, bool neg0, __nv_bfloat16* d1, int off1,
+                                               int w, int beta, double x, int e) {
+  long long R = fixed62(x, e);
+#pragma unroll 3
+  for (int t = 0; t < S; ++t) {
+    const int sh = 62 - beta * (t + 1);
+    long long q;
+    if (sh > 0) {
+      q = (R + (1ll << (sh - 1))) >> sh;
+      R -= q << sh;
+    } else {
+      q = R << -sh;
+      R = 0;
+    }
+    const float f = (float)(int)q;
+    d0[(size_t)t * w + off0] = __float2bfloat16_rn(neg0 ? -f : f);
+    d1[(size_t)t * w + off1] = __float2bfloat16_rn(f);
+  }
+}
+
 template <int S>
 __device__ __forceinline__ void write_digits1(__nv_bfloat16* row, int w, int off, int beta, double x, int e) {
   long long R = fixed62(x, e);
@@ -453,10 +504,8 @@ __device__ __forceinline__ void pack_tile(const OzPackDesc& p, int t, z64 (&tile
       } else {  // B' rows 2v = [Br | -Bi], 2v+1 = [Bi | Br]
         __nv_bfloat16* r0 = p.out + (size_t)(2 * v) * rowlen;
         __nv_bfloat16* r1 = r0 + rowlen;
-        write_digits2<S>(r0, p.w, kg, beta, z0.x, z1.x, ex[vv]);
-        write_digits2<S>(r0, p.w, k + kg, beta, -z0.y, -z1.y, ex[vv]);
-        write_digits2<S>(r1, p.w, kg, beta, z0.y, z1.y, ex[vv]);
-        write_digits2<S>(r1, p.w, k + kg, beta, z0.x, z1.x, ex[vv]);
+        write_digits2x<S>(r0, kg, false, r1, k + kg, p.w, beta, z0.x, z1.x, ex[vv]);  // Br
+        write_digits2x<S>(r0, k + kg, true, r1, kg, p.w, beta, z0.y, z1.y, ex[vv]);  // -Bi, Bi
       }
     }
     return;
@@ -473,10 +522,8 @@ __device__ __forceinline__ void pack_tile(const OzPackDesc& p, int t, z64 (&tile
     } else {
       __nv_bfloat16* r0 = p.out + (size_t)(2 * v) * rowlen;
       __nv_bfloat16* r1 = r0 + rowlen;
-      write_digits1<S>(r0, p.w, kg, beta, z.x, ex[vv]);
-      write_digits1<S>(r0, p.w, k + kg, beta, -z.y, ex[vv]);
-      write_digits1<S>(r1, p.w, kg, beta, z.y, ex[vv]);
-      write_digits1<S>(r1, p.w, k + kg, beta, z.x, ex[vv]);
+      write_digits1x<S>(r0, kg, false, r1, k + kg, p.w, beta, z.x, ex[vv]);  // Br
+      write_digits1x<S>(r0, k + kg, true, r1, kg, p.w, beta, z.y, ex[vv]);  // -Bi, Bi
     }
   }
 }

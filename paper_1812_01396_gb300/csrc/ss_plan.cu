@@ -277,12 +277,17 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
-    if (upd == UPD_EXACT_TC || upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
+    if (upd == UPD_EXACT_TC || upd == UPD_EXACT_ALL || upd == UPD_EXACT_FAR) ok = ok && oz_gemm(g, pack, cap, err, true);
     else gemm(g, true);
   };
   // the nb-deep updates inside an outer block (two-level blocking)
   auto inner_update = [&](const std::vector<GemmDesc>& g) {
     if (upd == UPD_EXACT_ALL) ok = ok && oz_gemm(g, pack, cap, err, true);
+    else gemm(g, true);
+  };
+  // the outer block's rows on the columns right of it (nb deep, wide)
+  auto far_update = [&](const std::vector<GemmDesc>& g) {
+    if (upd == UPD_EXACT_ALL || upd == UPD_EXACT_FAR) ok = ok && oz_gemm(g, pack, cap, err, true);
     else gemm(g, true);
   };
   const int np = (int)ds.size();
@@ -363,7 +368,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
           g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, K1, k0 + nbw, K1));
         }
         rowblock(k0, 1, maxc);
-        inner_update(g);
+        far_update(g);
       }
       // one trailing update of depth nbo
       std::vector<GemmDesc> g;

@@ -143,7 +143,9 @@ class Plan {
   // Arithmetic of the rank-nb trailing and back-substitution updates
   // (panels, pivots and triangular blocks always stay FP64).
   // UPD_EXACT_ALL: the nb-deep updates inside an outer block too.
-  enum Updates { UPD_FP64 = 0, UPD_EXACT_TC = 2, UPD_EXACT_ALL = 3 };
+  // UPD_EXACT_FAR: like UPD_EXACT_TC, and the outer block's rows on the columns
+  // right of it (nb deep, wide) also exact; the updates inside the block stay FP64.
+  enum Updates { UPD_FP64 = 0, UPD_EXACT_TC = 2, UPD_EXACT_ALL = 3, UPD_EXACT_FAR = 4 };
   // UPD_EXACT_TC slices the update operands into `pack` (cap bytes).
   // nbo > nb (a multiple of nb): two-level blocking; the depth-nbo
   // trailing and back-substitution updates use `upd`, the nb-deep updates

@@ -279,12 +279,13 @@ cudaError_t launch_tc_gemm(const TcDesc* d, const int* tile_start, int nprob, in
   return cudaGetLastError();
 }
 
-// Tensor map of a K-major BF16 matrix rows x kp (row stride kp elements), box 64 x 128, 128B swizzle.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int kp, int box_rows) {
+cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int kp, int box_rows, int ld) {
+  if (ld == 0) ld = kp;
+  if (ld < kp || (ld * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorInvalidValue;
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -294,7 +295,7 @@ cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int 
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
   const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,

@@ -100,7 +100,10 @@ int pack_tiles(int rows, int kp);
 size_t tc_smem_bytes();
 int tc_box_rows_a();
 int tc_box_rows_b();
-cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int kp, int box_rows);
+// Tensor map of a K-major BF16 matrix (rows x kp, row stride ld elements, ld = kp when 0;
+// ld * 2 must be a multiple of 16 bytes), box 64 x box_rows, 128-byte swizzle, zero fill
+// outside the matrix.
+cudaError_t encode_kmajor_map(CUtensorMap* map, const void* base, int rows, int kp, int box_rows, int ld = 0);
 
 void launch_pack_a(const PackDesc* d, const int* tile_start, int nprob, int total, int mode, cudaStream_t st);
 void launch_pack_b(const PackDesc* d, const int* tile_start, int nprob, int total, int mode, cudaStream_t st);

@@ -40,17 +40,29 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def test_mlp_forward_and_gradients_match_oracle(ss):
+@pytest.mark.parametrize("width,n_out,batch,tc", [
+    (48, 32, 12, True),      # one tile, ragged in every dimension
+    (48, 32, 12, False),     # the SIMT kernel on the same case
+    (136, 264, 200, True),   # 2 x 3 output tiles, ragged M / N / K tails, K = 19 through a padded row stride
+    (36, 18, 9, False),      # widths that are not multiples of 8 run on the SIMT kernel only
+])
+def test_mlp_forward_and_gradients_match_oracle(ss, width, n_out, batch, tc):
     import torch
     from paper_1812_01396_gb300 import warm
-    net = ss.MLP(19, 48, 32, 16, seed=3)
-    params = [p.astype(np.float32) for p in omlp.init_params(32, width=48, seed=4)]
+    net = ss.MLP(19, width, n_out, batch + 3, seed=3)
+    if (width % 8 or n_out % 8) and tc:
+        pytest.skip("tensor cores need multiples of 8")
+    if width % 8 or n_out % 8:
+        with pytest.raises(ss.SSError):
+            net.use_tensor_cores(True)
+    net.use_tensor_cores(tc)
+    params = [p.astype(np.float32) for p in omlp.init_params(n_out, width=width, seed=4)]
     params = [p + 0.05 * np.float32(i % 2) for i, p in enumerate(params)]   # non-zero biases
     net.set_params(params)
     rng = np.random.default_rng(2)
-    E, k = rng.uniform(-1, 1, 12), rng.uniform(0, np.pi, 12)
+    E, k = rng.uniform(-1, 1, batch), rng.uniform(0, np.pi, batch)
     x = warm.features(E, k)
-    t = rng.standard_normal((12, 32)).astype(np.float32)
+    t = rng.standard_normal((batch, n_out)).astype(np.float32)
     tx, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     y = net.forward(tx).cpu().numpy()
     net.train_step(tx, tt, 0.0)
@@ -61,6 +73,43 @@ def test_mlp_forward_and_gradients_match_oracle(ss):
     assert rel(y, yo) < 1e-2
     for i in range(6):
         assert rel(grads[i], go[i]) < 1e-2, (i, rel(grads[i], go[i]))
+    net.close()
+
+
+def test_mlp_tensor_cores_match_simt_and_step_time(ss, capsys):
+    """The warm-start network at its workload size (width 512, n_out 2 * 128^2,
+    batch 256): tensor-core and SIMT GEMMs give the same outputs and gradients
+    to BF16 rounding (both round the same operands, both accumulate in FP32);
+    reports the time of one training step on each."""
+    import torch
+    from paper_1812_01396_gb300 import warm
+    W, O, B = 512, 2 * 128 * 128, 256
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(warm.features(rng.uniform(-1, 1, B), rng.uniform(0, np.pi, B))).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, O)).astype(np.float32)).cuda()
+    out = {}
+    for tc in (True, False):
+        net = ss.MLP(19, W, O, B, seed=8)
+        net.use_tensor_cores(tc)
+        y = net.forward(x).cpu().numpy()
+        loss = net.train_step(x, t, 0.0)
+        g = net.get_grads()
+        for _ in range(3):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for _ in range(20):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        out[tc] = dict(y=y, loss=loss, g=g, ms=(time.time() - t0) / 20 * 1e3)
+        net.close()
+    assert rel(out[True]["y"], out[False]["y"]) < 1e-2
+    assert abs(out[True]["loss"] - out[False]["loss"]) < 1e-2 * out[False]["loss"]
+    for i in range(6):
+        assert rel(out[True]["g"][i], out[False]["g"][i]) < 2e-2, i
+    with capsys.disabled():
+        print("\nMLP training step (19 -> 512 -> 512 -> 32768, batch 256): tensor cores %.3f ms, SIMT %.3f ms"
+              % (out[True]["ms"], out[False]["ms"]))
 
 
 def test_mlp_training_reduces_loss(ss):
