@@ -286,9 +286,8 @@ const char* ss_noalloc_last_error(void);
  * changes the order of FP64 roundings only.
  * It also times the padded-work heuristic and the FP64 complex GEMM's five
  * tile shapes on a group of n_problems s_b x s_b x s_b products (FP64 path)
- * and on the LU's wide rank-nb update in the shape the chosen blocking issues
- * ((s_b - nb) x (3 s_b - nb) x nb for one level, (nbo - nb) x (3 s_b - nbo) x nb
- * for two), and uses the fastest for those classes of products (-1 in the
+ * and, for the LU's wide rank-nb updates, on the whole LU solve of the chosen
+ * blocking, and uses the fastest for those classes of products (-1 in the
  * cache: the heuristic).
  * cache_path (optional): a text file of lines "precision s_b n_problems nb
  * nbo upd ms" and "G precision s_b n_problems square_tile update_tile"; a

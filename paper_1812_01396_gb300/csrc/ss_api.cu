@@ -2397,8 +2397,10 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (auto& c : cands) {
-    if (e != cudaSuccess) break;
+  // one LU solve of the batch with blocking c and update tile shape var_up
+  // (-1: the heuristic), timed as the pipeline runs it (replayed from a CUDA
+  // graph captured on the first run); best of three after a warm-up run
+  auto time_lu = [&](const ss_handle::Tune& c, int var_up) {
     std::vector<LuDesc> ds;
     for (int p = 0; p < n_problems; ++p) {
       LuDesc L{};
@@ -2406,13 +2408,13 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
       ds.push_back(L);
     }
     Plan P;
-    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err, c.nbo)) continue;
+    P.set_gemm_variants(-1, var_up);
+    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err, c.nbo)) return -1.f;
     e = P.upload(st);
     float best_ms = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
       e = cudaMemcpyAsync(W, W0, tot * sizeof(z64), cudaMemcpyDeviceToDevice, st);
       cudaEventRecord(e0, st);
-      // timed as the pipeline runs it: replayed from a CUDA graph (captured on the first run)
       if (e == cudaSuccess) e = h->cfg.use_graphs ? P.replay(st, nullptr) : P.run(st, nullptr);
       cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -2420,14 +2422,21 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) best_ms = std::min(best_ms, ms);  // first run warms up
     }
-    c.ms = best_ms;
+    return best_ms;
+  };
+  for (auto& c : cands) {
+    if (e != cudaSuccess) break;
+    const float ms = time_lu(c, -1);
+    if (ms < 0.f) continue;
+    c.ms = ms;
     if (e == cudaSuccess && (best.nb < 0 || c.ms < best.ms)) best = c;
   }
-  // FP64 GEMM tile shapes: the products of full s x s blocks (FP64 path) and
-  // the LU's wide rank-nb updates in the shape the chosen blocking issues them
-  // (one level: (s - nb) x (3 s - nb) x nb; two levels: the outer block's rows
-  // right of it, (nbo - nb) x (3 s - nbo) x nb), each group of n_problems timed
-  // with the heuristic (-1) and with every tile shape; the fastest is kept
+  // FP64 GEMM tile shapes.  The products of full s x s blocks (FP64 path):
+  // one group of n_problems products timed with the heuristic (-1) and with
+  // every tile shape.  The LU's wide rank-nb updates: the whole LU solve of
+  // the chosen blocking timed with each shape for them (they come in several
+  // shapes: the outer block's rows right of it, the back substitution's rows
+  // above it).  The fastest replaces the padded-work heuristic.
   auto time_gemm = [&](const std::vector<GemmDesc>& g, bool lu_label) {
     int bv = -1;
     float bms = 1e30f;
@@ -2450,22 +2459,21 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     return bv;
   };
   if (e == cudaSuccess && best.nb > 0) {
-    std::vector<GemmDesc> gsq, gup;
-    const int nbw = std::min(best.nb, s_b);
-    for (int p = 0; p < n_problems; ++p) {
-      z64* Wp = W + p * per;
-      gsq.push_back(gdesc(s_b, s_b, s_b, plain(Wp, 3 * s_b), plain(Wp + s_b, 3 * s_b), Wp + 2 * s_b, 3 * s_b, ONE, ZERO));
-      if (best.nbo > nbw && best.nbo < s_b) {
-        const int K1 = best.nbo;
-        gup.push_back(gdesc(K1 - nbw, 3 * s_b - K1, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
-                            plain(Wp + K1, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + K1, 3 * s_b, MONE, ONE));
-      } else if (s_b > nbw) {
-        gup.push_back(gdesc(s_b - nbw, 3 * s_b - nbw, nbw, plain(Wp + (size_t)nbw * 3 * s_b, 3 * s_b),
-                            plain(Wp + nbw, 3 * s_b), Wp + (size_t)nbw * 3 * s_b + nbw, 3 * s_b, MONE, ONE));
+    if (prec == SS_FP64) {
+      std::vector<GemmDesc> gsq;
+      for (int p = 0; p < n_problems; ++p) {
+        z64* Wp = W + p * per;
+        gsq.push_back(gdesc(s_b, s_b, s_b, plain(Wp, 3 * s_b), plain(Wp + s_b, 3 * s_b), Wp + 2 * s_b, 3 * s_b, ONE, ZERO));
       }
+      best.gsq = time_gemm(gsq, false);
     }
-    best.gsq = prec == SS_FP64 ? time_gemm(gsq, false) : -1;
-    best.gup = gup.empty() ? -1 : time_gemm(gup, true);
+    float bms = best.ms;  // the heuristic's time from the blocking search
+    best.gup = -1;
+    for (int v = 0; v < zgemm_num_variants() && e == cudaSuccess; ++v) {
+      const float ms = time_lu(best, v);
+      if (e == cudaSuccess && ms >= 0.f && ms < bms) { bms = ms; best.gup = v; }
+    }
+    best.ms = bms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
