@@ -151,14 +151,16 @@ def test_warm_start_workload_report(ss, capsys):
         h.set_warm_start(net, 1, scale)
         Ev = -1.0 + (2 * np.arange(1024) + 1) / 1024.0
         kid = np.zeros(1024, np.int32)
-        torch.cuda.synchronize()
-        t0 = time.time()
-        g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
-        t_plain = time.time() - t0
-        t0 = time.time()
-        g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(1024), side=1, use_warm=True, warm_iters=8,
-                                               warm_tol=1e-10)
-        t_warm = time.time() - t0
+        t_plain = t_warm = float("inf")
+        for _ in range(2):  # best of two timed calls each
+            torch.cuda.synchronize()
+            t0 = time.time()
+            g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
+            t_plain = min(t_plain, time.time() - t0)
+            t0 = time.time()
+            g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(1024), side=1, use_warm=True, warm_iters=8,
+                                                   warm_tol=1e-10)
+            t_warm = min(t_warm, time.time() - t0)
     finally:
         h.close()
     errs = np.array([rel(a, b) for a, b in zip(g1, g0)])
@@ -199,14 +201,17 @@ def test_warm_start_gap_energies_report(ss, capsys):
         h.set_warm_start(net, 1, scale)
         Ev = np.linspace(41.0, 59.0, 512)
         kid = np.zeros(512, np.int32)
-        torch.cuda.synchronize()
-        t0 = time.time()
-        g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
-        t_plain = time.time() - t0
-        t0 = time.time()
-        g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(512), side=1, use_warm=True, warm_iters=8,
-                                               warm_tol=1e-10)
-        t_warm = time.time() - t0
+        # best of three timed calls each (host clock around the synchronous calls)
+        t_plain = t_warm = float("inf")
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            g0, it0, _, st0, _ = h.surface_gf(Ev, kid, side=1)
+            t_plain = min(t_plain, time.time() - t0)
+            t0 = time.time()
+            g1, it1, seeded, st1, _ = h.surface_gf(Ev, kid, np.zeros(512), side=1, use_warm=True, warm_iters=8,
+                                                   warm_tol=1e-10)
+            t_warm = min(t_warm, time.time() - t0)
     finally:
         h.close()
     errs = np.array([rel(a, b) for a, b in zip(g1, g0)])
