@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--partitions", type=int, default=1, help="partitions of every device (cfg.partitions)")
     ap.add_argument("--tournament", action="store_true",
                     help="tournament pivoting in the cluster LU panels (cfg.tournament_pivoting)")
+    ap.add_argument("--lu-lookahead", type=int, default=0, choices=(0, 1),
+                    help="side-stream trailing updates in the two-level LU (cfg.lu_lookahead)")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps of the per-kernel event-timed pass (kernel shares and the roofline)")
     ap.add_argument("--gemm", default=None, metavar="MxNxK",
@@ -626,7 +628,7 @@ def main():
         h = ss.Handle(n_b_max=a.n_b, s_b_max=a.s_b, max_points=P, max_inj=a.n_inj, device_ptrs=device_ptrs,
                       stream=stream.cuda_stream, precision=prec, profile=profile, use_graphs=0 if a.no_graphs else 1,
                       hermitian_sweeps=1 if a.hermitian else 0, partitions=a.partitions,
-                      tournament_pivoting=1 if a.tournament else 0)
+                      tournament_pivoting=1 if a.tournament else 0, lu_lookahead=a.lu_lookahead)
         with torch.cuda.stream(stream):
             for k, d in enumerate(devs):
                 if device_ptrs:
@@ -823,6 +825,7 @@ def main():
                        "sweep_factorisation": "L D L^H without pivoting" if a.hermitian else "pivoted LU",
                        "partitions": a.partitions,
                        "panel_pivoting": "tournament" if a.tournament else "partial",
+                       "lu_lookahead": a.lu_lookahead,
                        "n_inj": a.n_inj, "precision": "fp64" if head_prec == ss.SS_FP64 else "mixed (SS_MIXED_OZAKI)",
                        "parallelism": f"(E,k) shards x{world}",
                        "l2": "inputs larger than L2: per-step workspace "

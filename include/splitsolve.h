@@ -128,6 +128,14 @@ typedef struct {
                          two cluster barriers per panel instead of one per column.
                          Another stable pivot order; results change at rounding level.
                          Default 0 (partial pivoting).                                */
+  int lu_lookahead;     /* 1: in the two-level blocked LU the depth-nbo update of the
+                         columns right of the next outer block runs on a second stream
+                         while that block's panels are factored (row exchanges of those
+                         columns wait for their block's far phase).  The same operations
+                         in the same order on every element: results are bit-identical
+                         to 0.  Default 0: the persistent exact GEMM holds every SM's
+                         shared memory, so the panels cannot run beside it, and the
+                         split update and extra exchange pass cost more than they hide. */
 } ss_config;
 
 /* Fill *cfg with the defaults listed above (n_b_max = 64, s_b_max = 512,

@@ -49,6 +49,7 @@ class SSConfig(C.Structure):
         ("use_graphs", C.c_int), ("profile", C.c_int), ("partitions", C.c_int), ("memory_lean", C.c_int),
         ("hermitian_sweeps", C.c_int), ("obc", C.c_int), ("feast_radius", C.c_double),
         ("feast_points", C.c_int), ("feast_subspace", C.c_int), ("tournament_pivoting", C.c_int),
+        ("lu_lookahead", C.c_int),
     ]
 
 

@@ -345,7 +345,8 @@ void lu(ss_handle* h, Plan& P, const std::vector<LuDesc>& ds) {
   Plan::Updates upd = h->mixed() ? Plan::UPD_EXACT_TC : Plan::UPD_FP64;
   auto it = h->tune.find(smax);
   if (it != h->tune.end()) { nb = it->second.nb; nbo = it->second.nbo; upd = (Plan::Updates)it->second.upd; }
-  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo, h->cfg.tournament_pivoting))
+  if (!P.lu_solve(ds, nb, upd, h->pack, h->pack_bytes, h->tc_err, nbo, h->cfg.tournament_pivoting,
+                  h->cfg.lu_lookahead))
     h->plan_error = true;
 }
 // The sweep blocks D_i with cfg.hermitian_sweeps: LDL^H without pivoting,
@@ -2055,6 +2056,7 @@ void ss_config_default(ss_config* cfg) {
   cfg->feast_points = 16;
   cfg->feast_subspace = 0;
   cfg->tournament_pivoting = 0;
+  cfg->lu_lookahead = 0;
 }
 
 int ss_create(ss_handle** hp, const ss_config* cfg) {
@@ -2088,6 +2090,10 @@ int ss_create(ss_handle** hp, const ss_config* cfg) {
   }
   if (cfg->partitions < 1 || cfg->partitions > MAXP) {
     g_create_error = "partitions outside 1.." + std::to_string(MAXP);
+    return SS_ERR_ARG;
+  }
+  if (cfg->lu_lookahead != 0 && cfg->lu_lookahead != 1) {
+    g_create_error = "lu_lookahead must be 0 or 1";
     return SS_ERR_ARG;
   }
   int ndev = 0;
@@ -2409,7 +2415,9 @@ int ss_autotune(ss_handle* h, int s_b, int n_problems, const char* cache_path, i
     }
     Plan P;
     P.set_gemm_variants(-1, var_up);
-    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err, c.nbo)) return -1.f;
+    if (!P.lu_solve(ds, c.nb, (Plan::Updates)c.upd, h->pack, h->pack_bytes, h->tc_err, c.nbo, 0,
+                    h->cfg.lu_lookahead))
+      return -1.f;
     e = P.upload(st);
     float best_ms = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {

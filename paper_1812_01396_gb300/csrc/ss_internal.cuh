@@ -145,10 +145,12 @@ int lu_panel_width(int smax);
 // barriers per panel instead of one per column); others use partial pivoting.
 void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaStream_t st, int tournament = 0);
 // nbo > 0: two-level blocking with outer width nbo (the solve stops at the
-// outer block's end); far != 0: solve the columns right of the outer block
-// without swaps.
+// outer block's end); far: the column ranges and row exchanges (see
+// lu_rowblock_kernel); far 3 (every row exchange of the outer block on the
+// columns right of it) runs as one gather per column when its staging fits.
+// max_rows: the largest block s of the group.
 void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int far, int max_cols,
-                        cudaStream_t st);
+                        cudaStream_t st, int max_rows = 0);
 void launch_lu_backsub_diag(const LuDesc* d, int nprob, int k0, int nb, int max_rhs,
                             cudaStream_t st);
 // Hermitian LDL^H panel without pivoting (see ss_lu.cu); smax: largest block of the group.

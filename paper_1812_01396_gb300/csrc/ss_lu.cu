@@ -717,17 +717,16 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
   const int q = blockIdx.x * RB_THREADS + threadIdx.x;
   z64* __restrict__ w = d.w;
   const size_t ld = d.ldw;
-  int c;
-  if (far) {
-    if (q >= d.ncols - K1) return;
-    c = K1 + q;
-  } else {
-    // columns left of the outer block (left of the panel with one level)
-    // hold L factors nothing reads again: they are not swapped
-    const int c0 = nbo > 0 ? (k0 / nbo) * nbo : k0;
-    const int nout = d.ncols - nbw - c0;
-    if (q >= nout) return;
-    c = (c0 + q < k0) ? c0 + q : c0 + q + nbw;
+  // far 0: row exchanges on every column from the outer block on, L11^-1 on the
+  //        block's columns right of the panel;
+  // far 1: L11^-1 on the columns right of the outer block (exchanged before);
+  // far 2: as 0 with the exchanges limited to the outer block's columns;
+  // far 3: the row exchanges of every panel of the outer block, in order, on
+  //        the columns right of it, and nothing else (2 for each panel, then 3
+  //        once, then 1 for each panel: the same operations in the same order
+  //        on every column as 0 then 1, with the columns right of the block
+  //        untouched until its far phase)
+  auto exchange = [&](int c) {
     for (int j = 0; j < nbw; ++j) {
       const int p = piv[j];
       if (p != k0 + j) {
@@ -738,6 +737,34 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
         *b = t;
       }
     }
+  };
+  int c;
+  if (far == 3) {
+    if (nbo <= 0 || q >= d.ncols - K1) return;
+    c = K1 + q;
+    for (int r = (k0 / nbo) * nbo; r < K1; ++r) {
+      const int p = d.ipiv[r];
+      if (p != r) {
+        z64* a = w + (size_t)r * ld + c;
+        z64* b = w + (size_t)p * ld + c;
+        const z64 t = *a;
+        *a = *b;
+        *b = t;
+      }
+    }
+    return;
+  }
+  if (far == 1) {
+    if (q >= d.ncols - K1) return;
+    c = K1 + q;
+  } else {
+    // columns left of the outer block (left of the panel with one level)
+    // hold L factors nothing reads again: they are not exchanged
+    const int c0 = nbo > 0 ? (k0 / nbo) * nbo : k0;
+    const int nout = (far == 2 ? K1 : d.ncols) - nbw - c0;
+    if (q >= nout) return;
+    c = (c0 + q < k0) ? c0 + q : c0 + q + nbw;
+    exchange(c);
     if (c < k0 || c >= K1) return;
   }
   z64 x[NB];
@@ -763,6 +790,74 @@ __global__ void __launch_bounds__(RB_THREADS) lu_rowblock_kernel(const LuDesc* _
 #pragma unroll
   for (int j = 0; j < NB; ++j)
     if (j < nbw) w[(size_t)(k0 + j) * ld + c] = x[j];
+}
+
+// Every row exchange of the outer block [K0, K1) (pivots ipiv[K0 .. K1-1],
+// applied in order) on the columns right of it, as one permutation: thread 0
+// composes the exchanges on a map of rows K0 .. s-1 in shared memory and lists
+// the rows whose values move (at most 2 (K1 - K0)); then XC columns per CTA
+// read every moving row's source value and, after a barrier, write it to its
+// destination.  The same data movement as the exchanges one after the other,
+// with no chain of dependent loads.
+constexpr int XC = 8, XT = 256;
+constexpr size_t XSMEM_MAX = 96 * 1024;
+size_t exchange_smem(int max_rows, int nbo) {
+  return (size_t)max_rows * 4 + (size_t)4 * nbo * 4 + 16 + (size_t)2 * nbo * XC * sizeof(z64);
+}
+
+__global__ void __launch_bounds__(XT) lu_block_exchange_kernel(const LuDesc* __restrict__ descs, int K0, int nbo) {
+  const LuDesc d = descs[blockIdx.y];
+  if (d.active && __ldg(d.active) == 0) return;
+  const int s = d.s;
+  if (K0 >= s) return;
+  const int K1 = min(K0 + nbo, s);
+  const int cbase = K1 + blockIdx.x * XC;
+  if (cbase >= d.ncols) return;
+  extern __shared__ __align__(16) unsigned char xsm[];
+  int* map = reinterpret_cast<int*>(xsm);  // row K0 + i receives the values of row map[i]
+  int* dst = map + (s - K0);
+  int* src = dst + 2 * nbo;
+  z64* stage = reinterpret_cast<z64*>((reinterpret_cast<uintptr_t>(src + 2 * nbo) + 15) & ~uintptr_t(15));
+  __shared__ int naff;
+  for (int i = threadIdx.x; i < s - K0; i += XT) map[i] = K0 + i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int r = K0; r < K1; ++r) {
+      const int p = d.ipiv[r];
+      if (p != r && p > r && p < s) {
+        const int t = map[r - K0];
+        map[r - K0] = map[p - K0];
+        map[p - K0] = t;
+      }
+    }
+    int n = 0;
+    for (int r = K0; r < K1; ++r) {
+      if (map[r - K0] != r) { dst[n] = r; src[n] = map[r - K0]; ++n; }
+    }
+    for (int r = K0; r < K1; ++r) {
+      const int p = d.ipiv[r];
+      if (p >= K1 && p < s && map[p - K0] != p) {  // listed once: its entry is reset below
+        dst[n] = p;
+        src[n] = map[p - K0];
+        map[p - K0] = p;
+        ++n;
+      }
+    }
+    naff = n;
+  }
+  __syncthreads();
+  const int n = naff;
+  z64* __restrict__ w = d.w;
+  const size_t ld = d.ldw;
+  for (int e = threadIdx.x; e < n * XC; e += XT) {
+    const int c = cbase + e % XC;
+    if (c < d.ncols) stage[e] = w[(size_t)src[e / XC] * ld + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * XC; e += XT) {
+    const int c = cbase + e % XC;
+    if (c < d.ncols) w[(size_t)dst[e / XC] * ld + c] = stage[e];
+  }
 }
 
 // B_k = U_kk^-1 B_k on the right-hand-side columns (backward substitution
@@ -971,8 +1066,18 @@ void launch_lu_panel(const LuDesc* d, int nprob, int k0, int nb, int smax, cudaS
 }
 
 void launch_lu_rowblock(const LuDesc* d, int nprob, int k0, int nb, int nbo, int far, int max_cols,
-                        cudaStream_t st) {
+                        cudaStream_t st, int max_rows) {
   if (nprob <= 0 || max_cols <= 0) return;
+  if (far == 3 && nbo > 0 && max_rows > 0 && exchange_smem(max_rows, nbo) <= XSMEM_MAX) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(lu_block_exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XSMEM_MAX);
+      attr_set = true;
+    }
+    dim3 xgrid((max_cols + XC - 1) / XC, nprob);
+    lu_block_exchange_kernel<<<xgrid, XT, exchange_smem(max_rows, nbo), st>>>(d, (k0 / nbo) * nbo, nbo);
+    return;
+  }
   dim3 grid((max_cols + RB_THREADS - 1) / RB_THREADS, nprob);
   if (nb <= 8) lu_rowblock_kernel<8><<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);
   else if (nb <= 16) lu_rowblock_kernel<16><<<grid, RB_THREADS, 0, st>>>(d, k0, nb, nbo, far);

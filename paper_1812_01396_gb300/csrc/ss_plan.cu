@@ -273,7 +273,7 @@ bool Plan::tc_gemm(const std::vector<GemmDesc>& ds, int mode, unsigned char* pac
 }
 
 bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned char* pack, size_t cap, int* err,
-                    int nbo, int tournament) {
+                    int nbo, int tournament, int lookahead) {
   if (ds.empty()) return true;
   bool ok = true;
   auto update = [&](const std::vector<GemmDesc>& g) {
@@ -311,6 +311,7 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
     LaunchRec rr;
     rr.kind = K_LU_ROW;
     rr.off = off; rr.nprob = np; rr.k0 = k0; rr.nb = nb; rr.nbo = nbo; rr.ival = far; rr.maxc = maxc;
+    rr.cap = smax;  // rows of the largest block (the exchange gather's staging)
     recs_.push_back(rr);
   };
   auto panel = [&](int k0) {
@@ -337,9 +338,14 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
       update(g);
     }
   } else {
+    // lookahead needs the nb-deep updates off the packing buffer (FP64), which
+    // the side stream's exact update may be using meanwhile
+    const bool la = lookahead && upd != UPD_EXACT_ALL;
+    bool forked = false;  // a side-stream trailing update not yet joined
     for (int K0 = 0; K0 < smax; K0 += nbo) {
       const int kend = std::min(K0 + nbo, smax);
-      // nb-wide steps inside the outer block
+      // nb-wide steps inside the outer block (with lookahead: row exchanges on
+      // the block's own columns only; they touch nothing the side stream writes)
       for (int k0 = K0; k0 < kend; k0 += nb) {
         panel(k0);
         int maxc = 0;
@@ -347,15 +353,26 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
         for (auto& d : ds) {
           if (k0 >= d.s) continue;
           const int nbw = std::min(nb, d.s - k0), K1 = std::min(K0 + nbo, d.s);
-          maxc = std::max(maxc, d.ncols - nbw);
+          maxc = std::max(maxc, la ? K1 - nbw - K0 : d.ncols - nbw);
           const int m = d.s - k0 - nbw, n = K1 - k0 - nbw;
           if (m <= 0 || n <= 0) continue;
           g.push_back(upd_desc(d, m, n, nbw, k0 + nbw, k0, k0, k0 + nbw, k0 + nbw, k0 + nbw));
         }
-        rowblock(k0, 0, maxc);
+        rowblock(k0, la ? 2 : 0, maxc);
         inner_update(g);
       }
-      // the block's rows on the columns right of it
+      if (forked) {  // the columns right of this block are up to date from here on
+        join();
+        forked = false;
+      }
+      // the block's rows on the columns right of it (with lookahead: the row
+      // exchanges of all the block's panels on those columns first)
+      if (la) {
+        int maxc = 0;
+        for (auto& d : ds)
+          if (K0 < d.s) maxc = std::max(maxc, d.ncols - std::min(K0 + nbo, d.s));
+        rowblock(K0, 3, maxc);
+      }
       for (int k0 = K0; k0 < kend; k0 += nb) {
         int maxc = 0;
         std::vector<GemmDesc> g;
@@ -370,17 +387,32 @@ bool Plan::lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd, unsigned
         rowblock(k0, 1, maxc);
         far_update(g);
       }
-      // one trailing update of depth nbo
-      std::vector<GemmDesc> g;
+      // one trailing update of depth nbo; with lookahead split into the next
+      // outer block's columns (now) and the columns right of it (side stream)
+      std::vector<GemmDesc> g, gw;
       for (auto& d : ds) {
         if (K0 >= d.s) continue;
         const int K1 = std::min(K0 + nbo, d.s);
         const int m = d.s - K1, n = d.ncols - K1;
         if (m <= 0 || n <= 0) continue;
-        g.push_back(upd_desc(d, m, n, K1 - K0, K1, K0, K0, K1, K1, K1));
+        if (!la) {
+          g.push_back(upd_desc(d, m, n, K1 - K0, K1, K0, K0, K1, K1, K1));
+          continue;
+        }
+        const int K2 = std::min(K1 + nbo, d.s);
+        g.push_back(upd_desc(d, m, K2 - K1, K1 - K0, K1, K0, K0, K1, K1, K1));
+        if (d.ncols > K2) gw.push_back(upd_desc(d, m, d.ncols - K2, K1 - K0, K1, K0, K0, K2, K1, K2));
       }
       update(g);
+      if (!gw.empty()) {
+        fork();
+        const size_t mark = recs_.size();
+        update(gw);
+        to_side(mark);
+        forked = true;
+      }
     }
+    if (forked) join();
   }
   // backward substitution on the right-hand sides: panels right to left
   int maxrhs = 0;
@@ -503,6 +535,11 @@ void Plan::release() {
   if (dev_) cudaFree(dev_);
   dev_ = nullptr;
   devcap_ = 0;
+  if (side_) cudaStreamDestroy(side_);
+  if (fork_ev_) cudaEventDestroy(fork_ev_);
+  if (join_ev_) cudaEventDestroy(join_ev_);
+  side_ = nullptr;
+  fork_ev_ = join_ev_ = nullptr;
 }
 
 // Hash of everything a captured launch depends on except the descriptor
@@ -518,13 +555,19 @@ size_t Plan::signature() const {
     mix((unsigned)r.k0); mix((unsigned)r.nb); mix((unsigned)r.maxc); mix((unsigned)r.nbo);
     unsigned long long tb;
     std::memcpy(&tb, &r.tol, sizeof(tb));
-    mix(tb); mix((unsigned)r.cap); mix((unsigned)r.count); mix((unsigned)r.ival); mix(r.bytes);
+    mix(tb); mix((unsigned)r.cap); mix((unsigned)r.count); mix((unsigned)r.ival); mix(r.bytes); mix((unsigned)r.side);
     for (int i = 0; i < 6; ++i) mix((unsigned long long)(uintptr_t)r.p[i]);
   }
   return h;
 }
 
 cudaError_t Plan::upload(cudaStream_t st) {
+  if (!side_ && std::any_of(recs_.begin(), recs_.end(), [](const LaunchRec& r) { return r.kind == K_FORK; })) {
+    cudaError_t e = cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
   const size_t need = host_.size() ? host_.size() : 16;
   if (need > devcap_) {
     destroy_graph();
@@ -589,7 +632,16 @@ static double gemm_flops(const LaunchRec& r, const std::vector<unsigned char>& h
 
 cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
   long long n = 0;
+  const cudaStream_t main_st = st;
   for (const LaunchRec& r : recs_) {
+    if (r.kind == K_FORK || r.kind == K_JOIN) {
+      cudaError_t e = r.kind == K_FORK ? cudaEventRecord(fork_ev_, main_st) : cudaEventRecord(join_ev_, side_);
+      if (e == cudaSuccess)
+        e = r.kind == K_FORK ? cudaStreamWaitEvent(side_, fork_ev_, 0) : cudaStreamWaitEvent(main_st, join_ev_, 0);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    st = r.side ? side_ : main_st;
     Prof::Rec pr{};
     if (prof && r.kind != K_MEMSET) {
       pr.kind = r.kind;
@@ -623,7 +675,10 @@ cudaError_t Plan::run(cudaStream_t st, long long* nlaunch, Prof* prof) {
         n += (r.maxc - r.k0 - r.nb > 0) ? 2 : 1;
         break;
       case K_LU_ROW:
-        if (r.maxc > 0) { launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.nbo, r.ival, r.maxc, st); ++n; }
+        if (r.maxc > 0) {
+          launch_lu_rowblock((const LuDesc*)d, r.nprob, r.k0, r.nb, r.nbo, r.ival, r.maxc, st, r.cap);
+          ++n;
+        }
         break;
       case K_LU_BACK: launch_lu_backsub_diag((const LuDesc*)d, r.nprob, r.k0, r.nb, r.maxc, st); ++n; break;
       case K_FROB2: launch_frob2((const Norm1Desc*)d, r.nprob, r.maxc, st); ++n; break;

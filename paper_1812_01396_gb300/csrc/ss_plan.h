@@ -20,7 +20,10 @@ long long host_launch_calls();
 // Launch kinds; the numbering is also the `kind` argument of ss_profile_read.
 enum LaunchKind { K_GEMM = 0, K_FORM, K_LU_PANEL, K_LU_ROW, K_LU_BACK, K_NORM1, K_TRACE, K_CHECK,
                   K_FILL, K_PACK_A, K_PACK_B, K_TCGEMM, K_GEMM32, K_OZSCALE, K_OZPACK, K_OZGEMM, K_FROB2,
-                  K_GEMM_LU, K_OZGEMM_LU, K_LU_HPANEL, K_EIG, K_MEMSET };
+                  K_GEMM_LU, K_OZGEMM_LU, K_LU_HPANEL, K_EIG, K_MEMSET,
+                  // not launches: K_FORK makes the side stream wait for the main one, K_JOIN
+                  // the main stream for the side one (records with `side` set run on it)
+                  K_FORK, K_JOIN };
 
 struct LaunchRec {
   LaunchKind kind;
@@ -31,6 +34,7 @@ struct LaunchRec {
   int cap = 0, count = 0, ival = 0;
   void* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t bytes = 0;
+  int side = 0;  // 1: issued on the plan's side stream (between a K_FORK and a K_JOIN)
 };
 
 // Optional per-launch timing: a CUDA event pair around every launch, with
@@ -151,8 +155,13 @@ class Plan {
   // trailing and back-substitution updates use `upd`, the nb-deep updates
   // inside an outer block are FP64 unless upd is UPD_EXACT_ALL.
   // tournament: tournament pivoting in the cluster panels (see launch_lu_panel).
+  // lookahead (two-level blocking, nb-deep updates in FP64): the depth-nbo
+  // update of the columns right of the next outer block runs on the side stream
+  // while the next outer block's panels are factored; row exchanges of the
+  // columns right of a block wait for its far phase.  The same operations in
+  // the same order on every element: bit-identical results.
   bool lu_solve(const std::vector<LuDesc>& ds, int nb, Updates upd = UPD_FP64, unsigned char* pack = nullptr,
-                size_t cap = 0, int* err = nullptr, int nbo = 0, int tournament = 0);
+                size_t cap = 0, int* err = nullptr, int nbo = 0, int tournament = 0, int lookahead = 0);
   // Hermitian LDL^H without pivoting of the leading s x s block of every
   // problem (only its lower triangle is read), then the solve of the
   // right-hand-side columns s..ncols-1: panels of nb columns, trailing updates
@@ -235,8 +244,13 @@ class Plan {
   bool oz_gemm_group(const std::vector<GemmDesc>& ds, unsigned char* pack, size_t cap, int* err, bool lu_label);
   void release();
   void destroy_graph();
+  void fork() { LaunchRec r; r.kind = K_FORK; recs_.push_back(r); }
+  void join() { LaunchRec r; r.kind = K_JOIN; recs_.push_back(r); }
+  void to_side(size_t from) { for (size_t i = from; i < recs_.size(); ++i) recs_[i].side = 1; }
   std::vector<unsigned char> host_;
   std::vector<LaunchRec> recs_;
+  cudaStream_t side_ = nullptr;  // created by upload() for plans that fork
+  cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
   unsigned char* dev_ = nullptr;
   size_t devcap_ = 0;
   cudaGraphExec_t exec_ = nullptr;

@@ -101,3 +101,41 @@ def test_gemm_tile_tuning_is_recorded_and_changes_no_bit(ss, tmp_path):
     assert all(-1 <= int(v) <= 4 for v in g[0][4:6])  # -1: the heuristic was fastest
     assert np.array_equal(out[0][1], out[1][1])
     assert all(np.array_equal(a, b) for a, b in zip(out[0][0], out[1][0]))
+
+
+# LU lookahead: the depth-nbo update of the columns right of the next outer
+# block on a second stream, row exchanges of those columns deferred to the far
+# phase.  Every element sees the same operations in the same order, so the
+# results must not change by a single bit, eagerly or replayed from graphs.
+@pytest.mark.parametrize("nb,nbo,upd", [(16, 64, 2), (8, 32, 4), (16, 128, 2), (16, 64, 0)])
+def test_lu_lookahead_is_bit_identical(ss, tmp_path, nb, nbo, upd):
+    s_b, n_b = 300, 3
+    dev = synth.make_device(n_b, s_b, seed=71)[0]
+    inj = synth.make_injection(s_b, 3, seed=72, n_pts=3)
+    out = {}
+    for la in (0, 1):
+        cache = tmp_path / f"tune{la}.txt"
+        cache.write_text(f"3 {s_b} 4 {nb} {nbo} {upd} 1.0\n")
+        h = ss.Handle(n_b_max=n_b, s_b_max=s_b, max_points=3, max_inj=3, precision=3, lu_lookahead=la)
+        try:
+            assert h.autotune(s_b, 4, cache)[:3] == (nb, nbo, upd)
+            h.set_device(0, dev)
+            res = []
+            for Es in ([0.15, -0.35, 0.5], [0.25, -0.45, 0.6]):  # the second batch replays the graphs
+                sL, sR, _, st0, _ = h.self_energy(Es, [0, 0, 0])
+                xs, st1, _ = h.solve(Es, [0, 0, 0], [inj[0], inj[1], inj[2]])
+                T, _, st2, _ = h.transmission(Es, [0, 0, 0])
+                assert np.all(np.asarray(st0) == 0) and np.all(np.asarray(st1) == 0) and np.all(np.asarray(st2) == 0)
+                res.append(([np.asarray(a).copy() for a in sL] + [np.asarray(a).copy() for a in sR],
+                            [np.asarray(x).copy() for x in xs], np.asarray(T).copy()))
+        finally:
+            h.close()
+        out[la] = res
+    for a, b in zip(out[0], out[1]):
+        assert all(np.array_equal(u, v) for u, v in zip(a[0], b[0]))
+        assert all(np.array_equal(u, v) for u, v in zip(a[1], b[1]))
+        assert np.array_equal(a[2], b[2])
+    # and the lookahead result is the oracle's
+    for p, E in enumerate([0.15, -0.35, 0.5]):
+        ref = dense.solve_point(dev, E, inj[p])
+        assert dense.rel_T_err(float(out[1][0][2][p]), ref["T"]) < 1e-9
