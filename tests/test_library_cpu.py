@@ -67,6 +67,26 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert isinstance(lib.ss_last_error(None), bytes)
 
 
+@pytest.mark.parametrize("field,value", [
+    ("partitions", 0), ("partitions", 9), ("lu_lookahead", 2), ("lu_lookahead", -1),
+])
+def test_create_rejects_bad_options_before_touching_a_device(lib, field, value):
+    """Option checks run on the host before any CUDA call, and each names the
+    field in the error text."""
+    h = C.c_void_p()
+    cfg = ss.ss_config_default()
+    setattr(cfg, field, value)
+    assert lib.ss_create(C.byref(h), C.byref(cfg)) == ss.SS_ERR_ARG
+    assert h.value is None
+    assert field.encode() in lib.ss_last_error(None)
+
+
+def test_config_defaults_of_the_options(lib):
+    cfg = ss.ss_config_default()
+    assert (cfg.partitions, cfg.memory_lean, cfg.hermitian_sweeps, cfg.obc) == (1, 0, 0, ss.SS_OBC_DECIMATION)
+    assert (cfg.tournament_pivoting, cfg.lu_lookahead, cfg.use_graphs) == (0, 0, 1)
+
+
 def test_create_reports_missing_device(lib):
     import torch
     if torch.cuda.is_available():
