@@ -751,6 +751,15 @@ def main():
                     "tensor_pipe_issued_tflops": tensor, "tensor_pipe_issued_frac": tensor / pk,
                     "issued_over_algorithmic": g["issued"] / max(g["flops"], 1.0),
                     "avg_launch_ms": ms / launches, "share_of_kernel_time": ms / tot_ms}
+        # the second bound of the mixed step: the LU's nb-deep FP64 updates on the FP64 pipe
+        z = kern["zgemm_lu"]
+        if z["ms"] > 0:
+            zr = z["flops"] / (z["ms"] * 1e-3) / 1e12
+            roofline["fp64_lu_updates"] = {
+                "kernel": "zgemm_kernel (FP64 complex GEMM, the blocked LU's nb-deep updates)", "bound": "alu",
+                "achieved": zr, "peak": peak_fp64, "unit": "TFLOP/s", "frac": zr / peak_fp64,
+                "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 pipe)",
+                "share_of_kernel_time": z["ms"] / tot_ms}
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
